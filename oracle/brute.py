@@ -44,7 +44,10 @@ def rect(extents, red_level, op, prec, body, A=None, w=None, params=None):
             rflat = 0
             for l, i in enumerate(ri):
                 rflat = rflat * red_ext[l] + i
-            terms.append(_body(body, flat, rflat, A, w, params, is_int))
+            t = _body(body, flat, rflat, A, w, params, is_int)
+            if prec == "i32":
+                t = ((t + 2**31) % 2**32) - 2**31   # 32-bit nests: values modulo 2^32
+            terms.append(t)
         if op == "sum":
             v = sum(terms) if is_int else math.fsum(terms)
             if prec == "i32":

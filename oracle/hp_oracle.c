@@ -23,9 +23,10 @@
  *   - FP64 sums use Neumaier's compensated summation (Neumaier 1974, "Rundungs-
  *     fehleranalyse einiger Verfahren zur Summation endlicher Summen"), error
  *     about 2 u64 |s| + O(n u64^2) sum|t|.
- *   - Integer work is exact in int64 with overflow detection; a 32-bit integer
- *     sum is reported modulo 2^32, which is what any wrapping 32-bit adder
- *     produces in any order.
+ *   - Integer work is exact in int64 with overflow detection.  For 32-bit
+ *     integer nests body values and sums are reported modulo 2^32 (two's
+ *     complement), which is what any wrapping 32-bit adder produces in any
+ *     order; 64-bit nests widen int32 inputs and count overflowed outputs.
  *   - Every FP result is returned with sum|t| and sum t^2, so that errors can be
  *     stated per result against its conditioning.
  *
@@ -195,9 +196,13 @@ static double body_fp_exact(const nest_ctx *c, int64_t flat, int64_t rflat)
 
 static int64_t body_int_exact(const nest_ctx *c, int64_t flat, int64_t rflat);
 
+static int64_t wrap32(int64_t v);
+
+/* 32-bit integer nests compute body values modulo 2^32 as well */
 static int64_t body_int(const nest_ctx *c, int64_t flat, int64_t rflat)
 {
-    return (int64_t)mutated_sign(flat) * body_int_exact(c, flat, mutated_rflat(c, rflat));
+    int64_t v = (int64_t)mutated_sign(flat) * body_int_exact(c, flat, mutated_rflat(c, rflat));
+    return (c->int_bits == 32) ? wrap32(v) : v;
 }
 
 static int64_t body_int_exact(const nest_ctx *c, int64_t flat, int64_t rflat)
