@@ -1,0 +1,260 @@
+/*
+ * hp.h — C ABI of the hierarchical loop-nest executor for GB300 (sm_103a).
+ *
+ * A nest is a depth-d loop nest, rectangular or ragged (CSR), with a body
+ * evaluated once per iteration and a reduction at any level.  Each nest level
+ * is bound to one level of the GPU's hardware hierarchy (grid, thread-block
+ * cluster, CTA, warp, sub-warp, lane, sequential), the way the paper's
+ * level(...) clause selects "where to get the new parallelism from" (Sec. 3.1),
+ * and each reduction is carried out on the level it is bound to with that
+ * level's own means of communication (Sec. 2: shuffles at warp level, shared
+ * memory at CTA level, distributed shared memory at cluster level, a
+ * deterministic two-pass combine at grid level).
+ *
+ * Conventions for every entry point:
+ *   - Calls return an hp_status and never abort or exit.  On failure,
+ *     hp_last_error() returns a message for the calling thread.
+ *   - "device pointer" means memory of the current CUDA device (e.g. from
+ *     torch or cudaMalloc); "host pointer" means ordinary host memory.
+ *     The caller owns every buffer it passes; the library owns its own scratch
+ *     and frees it in the matching destroy call.
+ *   - stream is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Runs are asynchronous on that stream: inputs must stay valid,
+ *     and outputs must not be read, until the stream's work completes.
+ *   - The library performs no CPU fallback: when no GB300 is present, runs
+ *     fail with HP_ECUDA.
+ */
+#ifndef HP_H
+#define HP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HP_MAX_DEPTH 5
+
+typedef enum hp_status {
+    HP_OK = 0,
+    HP_EINVAL = 1,          /* invalid argument or illegal level map */
+    HP_ENOMEM = 2,          /* device or host allocation failed, or over budget */
+    HP_EBUSY = 3,           /* resource (serving slot, stream) in use */
+    HP_EAGAIN = 4,          /* not finished yet (serving poll) */
+    HP_ETIMEOUT = 5,        /* a bounded wait ran out (host or device side) */
+    HP_ECUDA = 6,           /* a CUDA call failed; message in hp_last_error() */
+    HP_EUNSUPPORTED = 7     /* legal request this build does not implement */
+} hp_status;
+
+/*
+ * Hardware levels (Sec. 3.1, level clause; Fig. 1 hierarchy, reduced to the
+ * levels CUDA exposes on GB300).  A nest level bound to level X has its
+ * iterations spread over the members of one X: GRID spreads over the clusters
+ * (or CTAs) of the grid, CLUSTER over the CTAs of a cluster, CTA over the
+ * warps of a CTA, WARP over the 32 lanes of a warp (or over its sub-warp
+ * groups when a deeper nest level is bound to SUBWARP), SUBWARP over the
+ * sub_width lanes of a sub-warp group (Sec. 3.8, level partitioning), LANE over
+ * the vector slots of one thread's 128-bit registers (the SIMD-in-register
+ * level at the bottom of Fig. 1), SEQ runs sequentially in one thread.
+ * Iterations left over after the members are used up are strip-mined: each
+ * member loops over its share (Sec. 3.4, "SPMD mode").
+ * A nest level also covers the hardware levels below its own down to the next
+ * nest level's (collapse, Sec. 3.1); consecutive nest levels bound to the same
+ * hardware level are collapsed into one.
+ */
+typedef enum hp_hw {
+    HP_HW_GRID = 0,
+    HP_HW_CLUSTER = 1,
+    HP_HW_CTA = 2,
+    HP_HW_WARP = 3,
+    HP_HW_SUBWARP = 4,
+    HP_HW_LANE = 5,
+    HP_HW_SEQ = 6,
+    HP_HW_AUTO = 7          /* let the planner choose (all levels must be AUTO) */
+} hp_hw;
+
+typedef enum hp_red_op {
+    HP_RED_SUM = 0,
+    HP_RED_MAX = 1,
+    HP_RED_MIN = 2,
+    HP_RED_HIST_COUNT = 3   /* CSR nests only: count histogram of col >> shift */
+} hp_red_op;
+
+/*
+ * Arithmetic of body and reduction.
+ *   HP_F32       FP32 inputs, plain FP32 accumulation (deterministic tree).
+ *   HP_F32_COMP  FP32 inputs, compensated FP32 accumulation at every level
+ *                (error-free product and sum transformations; Ogita-Rump-
+ *                Oishi Dot2), FP64 only in the final grid-level combine.
+ *   HP_I32       int32 inputs, int32 accumulation: sums are exact modulo 2^32.
+ *   HP_I64       int32 inputs widened to int64, int64 accumulation.
+ * Outputs: float for the FP precisions, int32_t / int64_t for the integer ones.
+ */
+typedef enum hp_prec {
+    HP_F32 = 0,
+    HP_F32_COMP = 1,
+    HP_I32 = 2,
+    HP_I64 = 3
+} hp_prec;
+
+/*
+ * Bodies (flat = row-major index over all levels, rflat = row-major index over
+ * the reduced levels red_level..depth-1):
+ *   LOAD        A[flat]                            in_dev = {A}
+ *   DOT_BCAST   A[flat] * w[rflat]                 in_dev = {A, w}
+ *   CSR_GATHER  val[e] * x[col[e]]  (CSR nests)    in_dev = {offsets, col, val, x [, hist_out]}
+ *   AFFINE      a + b * (flat mod m)               no inputs; hp_affine_params
+ *   GEOMETRIC   fl32(q^(flat mod m))  (FP sums)    no inputs; hp_geometric_params
+ * AFFINE and GEOMETRIC read no memory: they exercise a mapping at any size
+ * against closed forms.
+ */
+typedef enum hp_body {
+    HP_BODY_LOAD = 0,
+    HP_BODY_DOT_BCAST = 1,
+    HP_BODY_CSR_GATHER = 2,
+    HP_BODY_AFFINE = 3,
+    HP_BODY_GEOMETRIC = 4
+} hp_body;
+
+/* One entry per nest level.
+ *   hw         an hp_hw value.
+ *   sub_width  level-specific width: CLUSTER = CTAs per cluster (1..16),
+ *              CTA = warps per CTA (1..32), SUBWARP = lanes per group
+ *              (1, 2, 4, 8, 16, 32), LANE = vector slots (1 or 4);
+ *              0 = default (8, 8, -, 4).
+ *   tile       GRID level of a reduction: iterations per grid part (0 = auto);
+ *              ignored elsewhere. */
+typedef struct hp_level_map {
+    int32_t hw;
+    int32_t sub_width;
+    int64_t tile;
+} hp_level_map;
+
+typedef struct hp_affine_params {
+    int64_t a, b, m;        /* m >= 1 */
+} hp_affine_params;
+
+typedef struct hp_geometric_params {
+    double q;               /* the body is fl32(q^k), q^k formed in FP64 */
+    int64_t m;              /* 1 <= m <= 1024 */
+} hp_geometric_params;
+
+/* CSR nests: offsets int64[n_rows + 1] (device), col int32[nnz] (device),
+ * val float[nnz] (device), x float[n_cols] (device). */
+typedef struct hp_csr_params {
+    int64_t nnz;
+    int64_t n_cols;
+    int32_t hist_shift;     /* histogram bin of entry e: col[e] >> hist_shift */
+    int32_t fuse_hist;      /* SUM nests: 1 = also count the histogram in the same sweep into in_dev[4] */
+    int64_t n_bins;         /* histogram bins (col >> shift must be < n_bins) */
+} hp_csr_params;
+
+typedef struct hp_nest hp_nest;
+typedef struct hp_server hp_server;
+
+/*
+ * Create a nest and its execution plan (host only; touches no GPU).
+ *   depth        1..HP_MAX_DEPTH for rectangular nests, 2 for CSR nests.
+ *   extents      int64[depth], each >= 0 (host pointer); NULL for CSR nests.
+ *   csr_offsets  NULL for rectangular nests; for CSR nests any non-NULL value
+ *                marks the nest as ragged (the offsets themselves are passed
+ *                at run time in in_dev[0]).
+ *   n_rows       CSR nests: number of outer rows; ignored otherwise.
+ *   map          hp_level_map[depth] (host pointer), or NULL to let the
+ *                planner choose (same as all HP_HW_AUTO).
+ *   op           reduction operator; red_level r in [0, depth]: levels
+ *                0..r-1 index the outputs, levels r..depth-1 are reduced
+ *                (r == depth: pure map, one output per iteration).
+ *   body_params  hp_affine_params / hp_geometric_params / hp_csr_params for
+ *                those bodies, else NULL (copied; host pointer).
+ * Output layout: row-major over levels 0..r-1 (float / int32 / int64 per prec).
+ * Errors: HP_EINVAL for an illegal shape or map (message names the rule),
+ * HP_EUNSUPPORTED for a legal combination this build does not implement,
+ * HP_ENOMEM if the host object cannot be allocated.
+ */
+hp_status hp_nest_create(int depth, const int64_t *extents, const int64_t *csr_offsets, int64_t n_rows,
+                         const hp_level_map *map, hp_red_op op, int red_level, hp_prec prec, hp_body body,
+                         const void *body_params, hp_nest **out);
+
+/*
+ * Run a nest on a stream (Sec. 2 reduction, executed as planned).
+ *   in_dev   array of device pointers (host array), per the body's list.
+ *            Memory-reading bodies need 16-byte aligned inputs when the plan
+ *            uses 128-bit loads (hp_nest_describe reports "vec").
+ *   out_dev  device pointer to the outputs (overwritten, never accumulated).
+ * The first run on a device allocates the nest's scratch; later runs allocate
+ * nothing.  Asynchronous: returns after enqueueing.  Device-side errors
+ * (a bounded wait that ran out) are reported by hp_nest_check.
+ */
+hp_status hp_nest_run(hp_nest *n, const void *const *in_dev, void *out_dev, void *stream);
+
+/*
+ * End-to-end run with HOST buffers: copies the inputs to device staging
+ * buffers owned by the nest, runs, copies the outputs back, and waits for the
+ * stream.  in_host / out_host are host pointers (pinned memory is fastest).
+ * CSR nests are not supported here (HP_EUNSUPPORTED).
+ */
+hp_status hp_nest_run_host(hp_nest *n, const void *const *in_host, void *out_host, void *stream);
+
+/*
+ * Run many independent nests in one persistent launch (replayed from a cached
+ * CUDA graph).  nests[i], in_dev[i], out_dev[i] as for hp_nest_run.  All nests
+ * must be rectangular.  Each nest's outputs equal those of hp_nest_run on the
+ * same nest bit for bit (same reduction tree).
+ */
+hp_status hp_nest_run_batch(hp_nest *const *nests, const void *const *const *in_dev, void *const *out_dev,
+                            int count, void *stream);
+
+/* A-priori bound on the normalized error of each FP result of this nest
+ * (|got - exact| / max(|exact|, scale), scale as reported by the tests):
+ * 0 for integer precisions and MAX/MIN. */
+hp_status hp_nest_error_bound(const hp_nest *n, double *rel_bound);
+
+/* Write the plan as one line of JSON (levels, hardware binding, team, grid,
+ * vector width, kernels) into buf[len]; truncated if too small. */
+hp_status hp_nest_describe(const hp_nest *n, char *buf, size_t len);
+
+/* Wait for the stream, then read the nest's device error word (0 = none;
+ * non-zero = a device-side bounded wait ran out).  Returns HP_ETIMEOUT if the
+ * word is set, HP_OK otherwise. */
+hp_status hp_nest_check(hp_nest *n, void *stream, int32_t *device_error);
+
+void hp_nest_destroy(hp_nest *n);
+
+/* ---------------------------------------------------------------------- */
+/* Serving: continuous batching of nest requests under a device-memory budget. */
+
+/* mem_budget_bytes: admission budget (inputs + outputs + scratch of admitted
+ * requests); max_slots: requests resident at once; n_streams: CUDA streams the
+ * scheduler launches steps on. */
+hp_status hp_serve_create(size_t mem_budget_bytes, int max_slots, int n_streams, hp_server **out);
+
+/* Submit one request: a nest (shape and plan; must stay alive until polled
+ * done), its device inputs and output.  Returns a ticket. */
+hp_status hp_serve_submit(hp_server *s, const hp_nest *shape, const void *const *in_dev, void *out_dev,
+                          uint64_t *ticket);
+
+/* HP_OK when the request finished (its output is valid), HP_EAGAIN while
+ * pending, HP_ETIMEOUT if timeout_us elapsed (timeout_us < 0 waits without limit
+ * on the host; the device side never spins), or an error. */
+hp_status hp_serve_poll(hp_server *s, uint64_t ticket, int timeout_us);
+
+/* Latency percentiles (microseconds, arrival to observed completion) and
+ * throughput (requests/s) over all completed requests. */
+hp_status hp_serve_stats(const hp_server *s, double *p50_us, double *p99_us, double *p999_us,
+                         double *nests_per_s);
+
+void hp_serve_destroy(hp_server *s);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *hp_last_error(void);
+
+/* ABI version (major * 100 + minor). */
+int hp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HP_H */

@@ -1,0 +1,279 @@
+"""Thin ctypes binding of libhp.so (include/hp.h), same names as the C ABI.
+
+Argument marshalling only: every step of the nest runs in the library's CUDA
+kernels.  There is no CPU fallback: if libhp.so is missing the first call
+raises, and on a machine without a GPU runs return HP_ECUDA.
+
+Device buffers are passed as integer addresses (e.g. ``tensor.data_ptr()``);
+streams as integer ``cudaStream_t`` handles (``torch.cuda.current_stream().cuda_stream``)
+or 0 for the legacy default stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhp.so")
+
+# ---- enums (include/hp.h)
+HP_OK, HP_EINVAL, HP_ENOMEM, HP_EBUSY, HP_EAGAIN, HP_ETIMEOUT, HP_ECUDA, HP_EUNSUPPORTED = range(8)
+STATUS_NAMES = ["HP_OK", "HP_EINVAL", "HP_ENOMEM", "HP_EBUSY", "HP_EAGAIN", "HP_ETIMEOUT", "HP_ECUDA",
+                "HP_EUNSUPPORTED"]
+HP_HW_GRID, HP_HW_CLUSTER, HP_HW_CTA, HP_HW_WARP, HP_HW_SUBWARP, HP_HW_LANE, HP_HW_SEQ, HP_HW_AUTO = range(8)
+HP_RED_SUM, HP_RED_MAX, HP_RED_MIN, HP_RED_HIST_COUNT = range(4)
+HP_F32, HP_F32_COMP, HP_I32, HP_I64 = range(4)
+HP_BODY_LOAD, HP_BODY_DOT_BCAST, HP_BODY_CSR_GATHER, HP_BODY_AFFINE, HP_BODY_GEOMETRIC = range(5)
+HP_MAX_DEPTH = 5
+
+HW = {"grid": HP_HW_GRID, "cluster": HP_HW_CLUSTER, "cta": HP_HW_CTA, "warp": HP_HW_WARP,
+      "subwarp": HP_HW_SUBWARP, "lane": HP_HW_LANE, "seq": HP_HW_SEQ, "auto": HP_HW_AUTO}
+OPS = {"sum": HP_RED_SUM, "max": HP_RED_MAX, "min": HP_RED_MIN, "hist": HP_RED_HIST_COUNT}
+PRECS = {"f32": HP_F32, "f32_comp": HP_F32_COMP, "i32": HP_I32, "i64": HP_I64}
+BODIES = {"load": HP_BODY_LOAD, "dot_bcast": HP_BODY_DOT_BCAST, "csr_gather": HP_BODY_CSR_GATHER,
+          "affine": HP_BODY_AFFINE, "geometric": HP_BODY_GEOMETRIC}
+
+# every entry point include/hp.h declares
+EXPORTED = ["hp_nest_create", "hp_nest_run", "hp_nest_run_host", "hp_nest_run_batch", "hp_nest_error_bound",
+            "hp_nest_describe", "hp_nest_check", "hp_nest_destroy", "hp_serve_create", "hp_serve_submit",
+            "hp_serve_poll", "hp_serve_stats", "hp_serve_destroy", "hp_last_error", "hp_version"]
+
+
+class hp_level_map(ctypes.Structure):
+    _fields_ = [("hw", ctypes.c_int32), ("sub_width", ctypes.c_int32), ("tile", ctypes.c_int64)]
+
+
+class hp_affine_params(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_int64), ("b", ctypes.c_int64), ("m", ctypes.c_int64)]
+
+
+class hp_geometric_params(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_double), ("m", ctypes.c_int64)]
+
+
+class hp_csr_params(ctypes.Structure):
+    _fields_ = [("nnz", ctypes.c_int64), ("n_cols", ctypes.c_int64), ("hist_shift", ctypes.c_int32),
+                ("fuse_hist", ctypes.c_int32), ("n_bins", ctypes.c_int64)]
+
+
+class HPError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib() -> ctypes.CDLL:
+    """Load libhp.so (raises if it was not built: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2309_01906_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        p, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64
+        L.hp_nest_create.restype = i32
+        L.hp_nest_create.argtypes = [i32, p, p, i64, p, i32, i32, i32, i32, p, ctypes.POINTER(p)]
+        L.hp_nest_run.restype = i32
+        L.hp_nest_run.argtypes = [p, p, p, p]
+        L.hp_nest_run_host.restype = i32
+        L.hp_nest_run_host.argtypes = [p, p, p, p]
+        L.hp_nest_run_batch.restype = i32
+        L.hp_nest_run_batch.argtypes = [p, p, p, i32, p]
+        L.hp_nest_error_bound.restype = i32
+        L.hp_nest_error_bound.argtypes = [p, ctypes.POINTER(ctypes.c_double)]
+        L.hp_nest_describe.restype = i32
+        L.hp_nest_describe.argtypes = [p, ctypes.c_char_p, ctypes.c_size_t]
+        L.hp_nest_check.restype = i32
+        L.hp_nest_check.argtypes = [p, p, ctypes.POINTER(ctypes.c_int32)]
+        L.hp_nest_destroy.restype = None
+        L.hp_nest_destroy.argtypes = [p]
+        L.hp_serve_create.restype = i32
+        L.hp_serve_create.argtypes = [ctypes.c_size_t, i32, i32, ctypes.POINTER(p)]
+        L.hp_serve_submit.restype = i32
+        L.hp_serve_submit.argtypes = [p, p, p, p, ctypes.POINTER(u64)]
+        L.hp_serve_poll.restype = i32
+        L.hp_serve_poll.argtypes = [p, u64, i32]
+        L.hp_serve_stats.restype = i32
+        L.hp_serve_stats.argtypes = [p] + [ctypes.POINTER(ctypes.c_double)] * 4
+        L.hp_serve_destroy.restype = None
+        L.hp_serve_destroy.argtypes = [p]
+        L.hp_last_error.restype = ctypes.c_char_p
+        L.hp_last_error.argtypes = []
+        L.hp_version.restype = i32
+        L.hp_version.argtypes = []
+        _lib = L
+        return L
+
+
+def hp_last_error() -> str:
+    return lib().hp_last_error().decode()
+
+
+def hp_version() -> int:
+    return lib().hp_version()
+
+
+def _check(st: int, where: str):
+    if st != HP_OK:
+        raise HPError(st, where, hp_last_error())
+
+
+def _ptr_array(ptrs):
+    arr = (ctypes.c_void_p * max(1, len(ptrs)))()
+    for i, v in enumerate(ptrs):
+        arr[i] = ctypes.c_void_p(int(v)) if v else None
+    return arr
+
+
+def make_map(levels):
+    """levels: list of (hw, sub_width, tile) tuples or hw names -> hp_level_map array."""
+    arr = (hp_level_map * len(levels))()
+    for i, lv in enumerate(levels):
+        if isinstance(lv, str):
+            lv = (lv, 0, 0)
+        hw, sw, tile = (tuple(lv) + (0, 0))[:3]
+        arr[i].hw = HW[hw] if isinstance(hw, str) else int(hw)
+        arr[i].sub_width = int(sw)
+        arr[i].tile = int(tile)
+    return arr
+
+
+def hp_nest_create(depth, extents, csr_offsets, n_rows, level_map, op, red_level, prec, body, body_params=None):
+    """Returns an opaque nest handle (int).  extents: list of ints or None; level_map:
+    make_map() array or list or None; body_params: ctypes struct or None."""
+    ext = (ctypes.c_int64 * max(1, depth))(*(extents or [])) if extents is not None else None
+    mp = level_map if (level_map is None or isinstance(level_map, ctypes.Array)) else make_map(level_map)
+    bp = ctypes.byref(body_params) if body_params is not None else None
+    h = ctypes.c_void_p()
+    off = ctypes.c_void_p(int(csr_offsets)) if csr_offsets else None
+    st = lib().hp_nest_create(depth, ext, off, int(n_rows), mp, OPS.get(op, op), red_level, PRECS.get(prec, prec),
+                              BODIES.get(body, body), bp, ctypes.byref(h))
+    _check(st, "hp_nest_create")
+    return h.value
+
+
+def hp_nest_run(nest, in_ptrs, out_ptr, stream=0):
+    st = lib().hp_nest_run(nest, _ptr_array(in_ptrs), out_ptr or None, stream or None)
+    _check(st, "hp_nest_run")
+
+
+def hp_nest_run_host(nest, in_host_ptrs, out_host_ptr, stream=0):
+    st = lib().hp_nest_run_host(nest, _ptr_array(in_host_ptrs), out_host_ptr or None, stream or None)
+    _check(st, "hp_nest_run_host")
+
+
+def hp_nest_run_batch(nests, in_ptr_lists, out_ptrs, stream=0):
+    n = len(nests)
+    harr = (ctypes.c_void_p * max(1, n))(*nests)
+    keep = [_ptr_array(x) for x in in_ptr_lists]
+    inarr = (ctypes.c_void_p * max(1, n))(*[ctypes.cast(k, ctypes.c_void_p) for k in keep])
+    outarr = _ptr_array(out_ptrs)
+    st = lib().hp_nest_run_batch(harr, inarr, outarr, n, stream or None)
+    _check(st, "hp_nest_run_batch")
+
+
+def hp_nest_error_bound(nest) -> float:
+    v = ctypes.c_double()
+    _check(lib().hp_nest_error_bound(nest, ctypes.byref(v)), "hp_nest_error_bound")
+    return v.value
+
+
+def hp_nest_describe(nest) -> dict:
+    buf = ctypes.create_string_buffer(8192)
+    _check(lib().hp_nest_describe(nest, buf, len(buf)), "hp_nest_describe")
+    return json.loads(buf.value.decode())
+
+
+def hp_nest_check(nest, stream=0) -> int:
+    v = ctypes.c_int32()
+    st = lib().hp_nest_check(nest, stream or None, ctypes.byref(v))
+    if st not in (HP_OK, HP_ETIMEOUT):
+        _check(st, "hp_nest_check")
+    return v.value
+
+
+def hp_nest_destroy(nest):
+    if nest:
+        lib().hp_nest_destroy(nest)
+
+
+def hp_serve_create(mem_budget_bytes, max_slots, n_streams):
+    h = ctypes.c_void_p()
+    _check(lib().hp_serve_create(int(mem_budget_bytes), max_slots, n_streams, ctypes.byref(h)), "hp_serve_create")
+    return h.value
+
+
+def hp_serve_submit(server, nest, in_ptrs, out_ptr) -> int:
+    t = ctypes.c_uint64()
+    _check(lib().hp_serve_submit(server, nest, _ptr_array(in_ptrs), out_ptr or None, ctypes.byref(t)),
+           "hp_serve_submit")
+    return t.value
+
+
+def hp_serve_poll(server, ticket, timeout_us=0) -> int:
+    """Returns HP_OK (done), HP_EAGAIN (pending) or HP_ETIMEOUT; raises on errors."""
+    st = lib().hp_serve_poll(server, ticket, timeout_us)
+    if st not in (HP_OK, HP_EAGAIN, HP_ETIMEOUT):
+        _check(st, "hp_serve_poll")
+    return st
+
+
+def hp_serve_stats(server):
+    v = [ctypes.c_double() for _ in range(4)]
+    _check(lib().hp_serve_stats(server, *[ctypes.byref(x) for x in v]), "hp_serve_stats")
+    return {"p50_us": v[0].value, "p99_us": v[1].value, "p999_us": v[2].value, "nests_per_s": v[3].value}
+
+
+def hp_serve_destroy(server):
+    if server:
+        lib().hp_serve_destroy(server)
+
+
+class Nest:
+    """Convenience owner of one nest handle (destroyed on close / garbage collection)."""
+
+    def __init__(self, extents=None, red_level=0, op="sum", prec="f32", body="load", level_map=None,
+                 params=None, csr_rows=None):
+        self.handle = None
+        if csr_rows is not None:
+            self.depth = 2
+            self.handle = hp_nest_create(2, None, 1, csr_rows, level_map, op, red_level, prec, body, params)
+        else:
+            self.depth = len(extents)
+            self.handle = hp_nest_create(len(extents), list(extents), None, 0, level_map, op, red_level, prec, body,
+                                         params)
+
+    def run(self, in_ptrs, out_ptr, stream=0):
+        hp_nest_run(self.handle, in_ptrs, out_ptr, stream)
+
+    def run_host(self, in_ptrs, out_ptr, stream=0):
+        hp_nest_run_host(self.handle, in_ptrs, out_ptr, stream)
+
+    def describe(self) -> dict:
+        return hp_nest_describe(self.handle)
+
+    def error_bound(self) -> float:
+        return hp_nest_error_bound(self.handle)
+
+    def check(self, stream=0) -> int:
+        return hp_nest_check(self.handle, stream)
+
+    def close(self):
+        if self.handle:
+            hp_nest_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

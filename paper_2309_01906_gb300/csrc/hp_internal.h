@@ -1,0 +1,111 @@
+// hp_internal.h — plan structures shared by the library's translation units.
+//
+// The planner (plan.cpp) turns a nest descriptor and its level -> hardware map
+// into a RectPlan / CsrPlan; the kernels read the plan by value.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "hp.h"
+
+namespace hp {
+
+constexpr int kMaxV = HP_MAX_DEPTH;  // reduced virtual levels
+constexpr int kMaxM = 32;            // items per synchronisation round of a block team
+constexpr int kMaxWarps = 32;
+constexpr int kGeoMax = 1024;        // GEOMETRIC table entries
+
+// Hardware scopes, coarse to fine (same order and values as hp_hw).
+enum Scope : int32_t { S_GRID = 0, S_CLUSTER = 1, S_CTA = 2, S_WARP = 3, S_SUB = 4, S_LANE = 5, S_SEQ = 6 };
+
+// Who cooperates on one output.
+enum Team : int32_t {
+  TEAM_BLOCK = 0,  // a cluster of C CTAs (C = 1: one CTA): reduction via shuffle, smem, DSMEM
+  TEAM_LANES = 1,  // a group of L lanes of one warp (L = 32: a warp; L = 1: a thread)
+  TEAM_MAP = 2,    // no reduction (red_level == depth): one output per iteration
+};
+
+// Everything the rectangular executor needs; passed by value to the kernels.
+struct RectPlan {
+  int64_t O;               // number of outputs
+  int64_t R;               // reduced elements per output
+  int64_t items;           // work items = O * G
+  int64_t tile;            // iterations of virtual level 0 per grid part (split only)
+  int64_t vn[kMaxV];       // extent of each reduced virtual level
+  int64_t vstride[kMaxV];  // element stride of each reduced virtual level
+  int32_t vP[kMaxV];       // parallel slots of each reduced virtual level
+  // slot of level v = rank*cr + warp*cw + grp*cg + lig*cl (+ vec for the vector level)
+  int32_t cr[kMaxV], cw[kMaxV], cg[kMaxV], cl[kMaxV];
+  int32_t nv;              // number of reduced virtual levels (0 when R == 1 via no levels)
+  int32_t split;           // 1: virtual level 0 is split over G grid parts
+  int32_t team;            // Team
+  int32_t C;               // CTAs per cluster (TEAM_BLOCK)
+  int32_t W;               // warps per CTA
+  int32_t L;               // lanes per team (TEAM_LANES)
+  int32_t grp_lanes;       // lanes per sub-warp group inside the team (32: none)
+  int32_t V;               // vector slots per thread on the innermost level (1 or 4)
+  int32_t G;               // grid parts per output
+  int32_t M;               // items per round (TEAM_BLOCK)
+  int32_t body;            // hp_body
+  int32_t geo_m;
+  int64_t aff_a, aff_b, aff_m;
+};
+
+// Host-side description of one rectangular nest's plan.
+struct NestPlan {
+  int depth = 0;
+  int red_level = 0;
+  int64_t ext[HP_MAX_DEPTH] = {0};
+  hp_level_map map[HP_MAX_DEPTH] = {};
+  bool auto_map = false;
+  hp_red_op op = HP_RED_SUM;
+  hp_prec prec = HP_F32;
+  hp_body body = HP_BODY_LOAD;
+  RectPlan rp = {};
+  int64_t total = 0;                 // iterations
+  int n_inputs = 0;                  // device inputs the body reads
+  int64_t in_elems[2] = {0, 0};      // elements of each input
+  size_t in_elem_bytes = 4;
+  size_t out_elem_bytes = 4;
+  std::vector<float> geo_table;      // GEOMETRIC body values fl32(q^k), k < m
+  std::string kernel;                // name of the kernel family the plan runs
+};
+
+// CSR plan (ragged 2-level nests).
+struct CsrPlan {
+  int64_t n_rows = 0, nnz = 0, n_cols = 0, n_bins = 0;
+  int32_t hist_shift = 0;
+  int32_t fuse_hist = 0;
+  hp_red_op op = HP_RED_SUM;
+  hp_prec prec = HP_F32;
+};
+
+// Launch geometry, fixed at the first run on a device.
+struct LaunchCfg {
+  bool ready = false;
+  int device = -1;
+  int sms = 0;
+  int grid = 0;        // CTAs
+  int threads = 0;     // per CTA
+  int cluster = 1;     // CTAs per cluster
+  int combine_grid = 0;
+  int M = 1;           // items per round of a block team
+};
+
+// Validate a rectangular nest and build its plan.  Returns HP_OK or an error
+// with a message in *why.
+hp_status plan_rect(int depth, const int64_t* extents, const hp_level_map* map, hp_red_op op, int red_level,
+                    hp_prec prec, hp_body body, const void* body_params, NestPlan* out, std::string* why);
+
+std::string describe_plan(const NestPlan& p);
+
+// A-priori bound on |got - exact| / sum|t| for one FP result of the plan.
+double error_bound_rect(const NestPlan& p);
+
+// Thread-local last-error message.
+void set_error(const std::string& msg);
+hp_status fail(hp_status st, const std::string& msg);
+
+}  // namespace hp

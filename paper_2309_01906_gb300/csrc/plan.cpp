@@ -1,0 +1,430 @@
+// plan.cpp — validation of nest descriptors and level -> hardware maps, and
+// lowering of a map onto the executor's team / slot / grid-part structure.
+// Pure host code: creating a nest never touches the GPU.
+//
+// Lowering (Sec. 3.1 level clause with collapse; Sec. 3.3 reserve: outer nest
+// levels take the coarser hardware levels, inner ones the finer; Sec. 3.4
+// strip-mining of the iterations left over; Sec. 3.8 sub-warp partitions):
+//   * consecutive nest levels bound to the same hardware level collapse into
+//     one virtual level; a virtual level covers its hardware level and every
+//     finer one down to the next virtual level's;
+//   * the first reduced level's hardware level decides the team that combines
+//     one output: a cluster or CTA (TEAM_BLOCK), a warp, a sub-warp group or a
+//     single thread (TEAM_LANES);
+//   * within a virtual level, iteration x goes to slot x mod P (finest hardware
+//     coordinate fastest, so neighbouring lanes read neighbouring elements) and
+//     step x div P; a reduced level bound to GRID is cut into G contiguous
+//     parts that are combined by a second, fixed-order pass.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <sstream>
+
+#include "hp_internal.h"
+
+namespace hp {
+
+namespace {
+thread_local std::string g_last_error;
+
+const char* hw_name(int hw) {
+  static const char* names[] = {"grid", "cluster", "cta", "warp", "subwarp", "lane", "seq", "auto"};
+  return (hw >= 0 && hw <= 7) ? names[hw] : "?";
+}
+
+const char* team_name(int t) {
+  return t == TEAM_BLOCK ? "block" : t == TEAM_LANES ? "lanes" : "map";
+}
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Auto-map heuristics assume a full GB300 (152 SMs); the grid itself is sized
+// from the real device at the first run.
+constexpr int64_t kAssumedSMs = 152;
+}  // namespace
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+hp_status fail(hp_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+const std::string& last_error_string() { return g_last_error; }
+
+static void auto_map(const NestPlan& p, hp_level_map* m) {
+  const int d = p.depth, r = p.red_level;
+  for (int l = 0; l < d; ++l) m[l] = {HP_HW_GRID, 0, 0};
+  if (r == d) return;
+  int64_t O = 1, R = 1;
+  for (int l = 0; l < r; ++l) O *= p.ext[l];
+  for (int l = r; l < d; ++l) R *= p.ext[l];
+  int red_hw;
+  int sub = 0;
+  if (R >= 4096) {
+    red_hw = (O < 2 * kAssumedSMs && R >= 65536) ? HP_HW_GRID : HP_HW_CTA;
+  } else if (R >= 128) {
+    red_hw = HP_HW_WARP;
+  } else if (R >= 8) {
+    red_hw = HP_HW_SUBWARP;
+    sub = 2;
+    while (sub < 16 && sub * 4 * 2 <= R) sub *= 2;
+  } else {
+    red_hw = HP_HW_SEQ;
+  }
+  // all reduced levels collapse into one contiguous virtual level
+  for (int l = r; l < d; ++l) m[l] = {red_hw, red_hw == HP_HW_SUBWARP ? sub : 0, 0};
+  if (r == 0 && red_hw == HP_HW_SUBWARP) {
+    // a single output: one sub-warp group would leave the rest of the warp idle
+    for (int l = r; l < d; ++l) m[l] = {HP_HW_WARP, 0, 0};
+  }
+}
+
+hp_status plan_rect(int depth, const int64_t* extents, const hp_level_map* map, hp_red_op op, int red_level,
+                    hp_prec prec, hp_body body, const void* body_params, NestPlan* out, std::string* why) {
+  auto bad = [&](const std::string& s) {
+    *why = s;
+    return HP_EINVAL;
+  };
+  if (depth < 1 || depth > HP_MAX_DEPTH) return bad("depth must be in [1, 5]");
+  if (!extents) return bad("extents is NULL");
+  if (red_level < 0 || red_level > depth) return bad("red_level must be in [0, depth]");
+  if (op != HP_RED_SUM && op != HP_RED_MAX && op != HP_RED_MIN)
+    return bad("rectangular nests reduce with SUM, MAX or MIN (HIST_COUNT is for CSR nests)");
+  if (prec < HP_F32 || prec > HP_I64) return bad("unknown precision");
+  if (body != HP_BODY_LOAD && body != HP_BODY_DOT_BCAST && body != HP_BODY_AFFINE && body != HP_BODY_GEOMETRIC)
+    return bad("rectangular nests take the LOAD, DOT_BCAST, AFFINE or GEOMETRIC body");
+  NestPlan p;
+  p.depth = depth;
+  p.red_level = red_level;
+  p.op = op;
+  p.prec = prec;
+  p.body = body;
+  int64_t total = 1;
+  for (int l = 0; l < depth; ++l) {
+    if (extents[l] < 0) return bad("extents must be >= 0");
+    p.ext[l] = extents[l];
+    int64_t t;
+    if (__builtin_mul_overflow(total, extents[l], &t) || t > (int64_t(1) << 62))
+      return bad("iteration space exceeds 2^62");
+    total = t;
+  }
+  p.total = total;
+  RectPlan& rp = p.rp;
+  std::memset(&rp, 0, sizeof(rp));
+  rp.body = body;
+  if (body == HP_BODY_AFFINE) {
+    if (!body_params) return bad("AFFINE body needs hp_affine_params");
+    auto* a = static_cast<const hp_affine_params*>(body_params);
+    if (a->m < 1) return bad("AFFINE: m must be >= 1");
+    rp.aff_a = a->a;
+    rp.aff_b = a->b;
+    rp.aff_m = a->m;
+  } else if (body == HP_BODY_GEOMETRIC) {
+    if (prec != HP_F32 && prec != HP_F32_COMP) return bad("GEOMETRIC body is an FP body");
+    if (op != HP_RED_SUM) return bad("GEOMETRIC body is for sums");
+    if (!body_params) return bad("GEOMETRIC body needs hp_geometric_params");
+    auto* g = static_cast<const hp_geometric_params*>(body_params);
+    if (g->m < 1 || g->m > kGeoMax) return bad("GEOMETRIC: m must be in [1, 1024]");
+    if (!std::isfinite(g->q)) return bad("GEOMETRIC: q must be finite");
+    rp.geo_m = static_cast<int32_t>(g->m);
+    p.geo_table.resize(g->m);
+    double v = 1.0;
+    for (int64_t k = 0; k < g->m; ++k) {
+      p.geo_table[k] = static_cast<float>(v);
+      v *= g->q;
+    }
+  }
+  p.n_inputs = body == HP_BODY_LOAD ? 1 : body == HP_BODY_DOT_BCAST ? 2 : 0;
+  const bool int_prec = prec == HP_I32 || prec == HP_I64;
+  p.in_elem_bytes = 4;
+  p.out_elem_bytes = prec == HP_I64 ? 8 : 4;
+  (void)int_prec;
+
+  // ---- the level map
+  bool all_auto = (map == nullptr);
+  if (map) {
+    all_auto = true;
+    bool any_auto = false;
+    for (int l = 0; l < depth; ++l) {
+      if (map[l].hw == HP_HW_AUTO) any_auto = true;
+      else all_auto = false;
+    }
+    if (any_auto && !all_auto) return bad("HP_HW_AUTO must be given for every level or for none");
+  }
+  p.auto_map = all_auto;
+  if (all_auto) auto_map(p, p.map);
+  else
+    for (int l = 0; l < depth; ++l) p.map[l] = map[l];
+
+  const hp_level_map* m = p.map;
+  for (int l = 0; l < depth; ++l) {
+    if (m[l].hw < HP_HW_GRID || m[l].hw > HP_HW_SEQ) return bad("level " + std::to_string(l) + ": unknown hardware level");
+    if (l > 0 && m[l].hw < m[l - 1].hw)
+      return bad("level " + std::to_string(l) + " is bound to a coarser hardware level than level " +
+                 std::to_string(l - 1) + " (inner levels take finer hardware, Sec. 3.3 reserve)");
+    if (m[l].tile < 0) return bad("tile must be >= 0");
+  }
+  // widths
+  int C = 1, W = 8, grp_lanes = 32, Vreq = 4;
+  bool has_cluster = false, has_cta = false, has_sub = false, has_lane_map = false;
+  for (int l = 0; l < depth; ++l) {
+    const int hw = m[l].hw, sw = m[l].sub_width;
+    if (hw == HP_HW_CLUSTER && !has_cluster) {
+      has_cluster = true;
+      C = sw ? sw : 8;
+      if (C < 1 || C > 16) return bad("CLUSTER sub_width (CTAs per cluster) must be in [1, 16]");
+    } else if (hw == HP_HW_CLUSTER && sw && sw != C) {
+      return bad("all levels bound to CLUSTER must give the same cluster size");
+    }
+    if (hw == HP_HW_CTA && !has_cta) {
+      has_cta = true;
+      W = sw ? sw : 8;
+      if (W < 1 || W > kMaxWarps) return bad("CTA sub_width (warps per CTA) must be in [1, 32]");
+    } else if (hw == HP_HW_CTA && sw && sw != W) {
+      return bad("all levels bound to CTA must give the same warp count");
+    }
+    if (hw == HP_HW_SUBWARP) {
+      if (!is_pow2(sw) || sw > 32) return bad("SUBWARP sub_width must be 1, 2, 4, 8, 16 or 32");
+      if (has_sub && sw != grp_lanes) return bad("all levels bound to SUBWARP must give the same width");
+      has_sub = true;
+      grp_lanes = sw;
+    }
+    if (hw == HP_HW_LANE && !has_lane_map) {
+      has_lane_map = true;
+      Vreq = sw ? sw : 4;
+      if (Vreq != 1 && Vreq != 4) return bad("LANE sub_width (vector slots) must be 1 or 4");
+    }
+  }
+  const int d = depth, r = red_level;
+  int64_t O = 1, R = 1;
+  for (int l = 0; l < r; ++l) O *= p.ext[l];
+  for (int l = r; l < d; ++l) R *= p.ext[l];
+  rp.O = O;
+  rp.R = R;
+  rp.W = W;
+  rp.C = 1;
+  rp.grp_lanes = grp_lanes;
+  rp.V = 1;
+  rp.G = 1;
+  rp.L = 32;
+  rp.M = 1;
+  p.in_elems[0] = total;
+  p.in_elems[1] = body == HP_BODY_DOT_BCAST ? R : 0;
+
+  if (r == d) {
+    rp.team = TEAM_MAP;
+    rp.items = O;
+    rp.nv = 0;
+    rp.V = (body == HP_BODY_LOAD || body == HP_BODY_DOT_BCAST) ? 4 : 1;
+    p.kernel = "rect_map";
+    *out = p;
+    return HP_OK;
+  }
+
+  // ---- team
+  const int T = m[r].hw;
+  for (int l = 0; l < r; ++l) {
+    if (m[l].hw == T && T != HP_HW_GRID)
+      return bad("output level " + std::to_string(l) + " and the first reduced level are both bound to " +
+                 hw_name(T) + ": a reduction must sit below the output levels it serves (only GRID may split one)");
+  }
+  if (T <= HP_HW_CTA) {
+    rp.team = TEAM_BLOCK;
+    // the cluster is the team when a reduced level covers the cluster scope
+    bool red_covers_cluster = false;
+    for (int l = r; l < d; ++l) {
+      const int lo = m[l].hw;
+      const int hi = (l + 1 < d) ? m[l + 1].hw : HP_HW_SEQ + 1;
+      if (lo <= HP_HW_CLUSTER && HP_HW_CLUSTER < hi) red_covers_cluster = true;
+    }
+    rp.C = (red_covers_cluster && has_cluster) ? C : 1;
+    rp.L = 32;
+  } else {
+    rp.team = TEAM_LANES;
+    rp.L = (T == HP_HW_WARP) ? 32 : (T == HP_HW_SUBWARP) ? grp_lanes : 1;
+    rp.C = 1;
+  }
+  if (rp.team == TEAM_LANES && T == HP_HW_SUBWARP) {
+    // the sub-warp group is the team; no finer groups inside
+  }
+
+  // ---- reduced virtual levels
+  struct VL {
+    int hw;
+    int64_t n;
+    int64_t stride;
+    int first, last;
+  };
+  std::vector<VL> vls;
+  for (int l = r; l < d; ++l) {
+    if (!vls.empty() && vls.back().hw == m[l].hw) {
+      vls.back().n *= p.ext[l];
+      vls.back().last = l;
+    } else {
+      vls.push_back({m[l].hw, p.ext[l], 1, l, l});
+    }
+  }
+  {
+    int64_t s = 1;
+    for (int v = static_cast<int>(vls.size()) - 1; v >= 0; --v) {
+      vls[v].stride = s;
+      s *= vls[v].n;
+    }
+  }
+  const int nv = static_cast<int>(vls.size());
+  if (nv > kMaxV) return bad("too many reduced levels");
+  rp.nv = nv;
+
+  // which virtual level covers the LANE scope, and does it get vector slots?
+  int lane_level = -1;
+  for (int v = 0; v < nv; ++v) {
+    const int lo = vls[v].hw;
+    const int hi = (v + 1 < nv) ? vls[v + 1].hw : HP_HW_SEQ + 1;
+    if (lo <= HP_HW_LANE && HP_HW_LANE < hi) lane_level = v;
+  }
+  int V = 1;
+  if (lane_level == nv - 1) {
+    V = Vreq;
+    // vector slots fold V consecutive iterations at once: the innermost run
+    // must be a whole number of vectors (for memory bodies: 128-bit loads)
+    if ((vls[nv - 1].n % V) != 0) V = 1;
+  }
+  rp.V = V;
+
+  // split over the grid
+  rp.split = 0;
+  rp.G = 1;
+  rp.tile = 0;
+  if (vls[0].hw == HP_HW_GRID) {
+    rp.split = 1;
+    const int64_t n0 = vls[0].n;
+    int64_t tile = 0;
+    for (int l = vls[0].first; l <= vls[0].last; ++l)
+      if (m[l].tile > 0) tile = m[l].tile;
+    if (tile <= 0) {
+      // aim at about two block teams per SM over all outputs
+      int64_t want_parts = std::max<int64_t>(1, (2 * kAssumedSMs + O - 1) / std::max<int64_t>(O, 1));
+      want_parts = std::min<int64_t>(want_parts, std::max<int64_t>(1, n0 / 4096));
+      tile = (n0 + want_parts - 1) / std::max<int64_t>(want_parts, 1);
+    }
+    if (nv == 1 && V > 1) tile = (tile + V - 1) / V * V;
+    if (tile < 1) tile = 1;
+    int64_t G = n0 > 0 ? (n0 + tile - 1) / tile : 1;
+    if (G > (int64_t(1) << 30)) return bad("too many grid parts");
+    rp.G = static_cast<int32_t>(G);
+    rp.tile = tile;
+  }
+
+  // slot coefficients (finest scope fastest)
+  const bool team_block = rp.team == TEAM_BLOCK;
+  for (int v = 0; v < nv; ++v) {
+    const int lo = vls[v].hw;
+    const int hi = (v + 1 < nv) ? vls[v + 1].hw : HP_HW_SEQ + 1;
+    int64_t mult = (v == nv - 1) ? V : 1;  // vector slots are the finest coordinate of the innermost level
+    rp.cr[v] = rp.cw[v] = rp.cg[v] = rp.cl[v] = 0;
+    for (int s = std::min(hi - 1, static_cast<int>(HP_HW_LANE)); s >= lo; --s) {
+      switch (s) {
+        case HP_HW_LANE:
+          break;  // handled by V on the innermost level; 1 slot elsewhere
+        case HP_HW_SUBWARP:
+          if (has_sub && (team_block || T <= HP_HW_SUBWARP)) {
+            rp.cl[v] = static_cast<int32_t>(mult);
+            mult *= grp_lanes;
+          }
+          break;
+        case HP_HW_WARP:
+          if (team_block || T <= HP_HW_WARP) {
+            if (has_sub) {
+              rp.cg[v] = static_cast<int32_t>(mult);
+              mult *= 32 / grp_lanes;
+            } else {
+              rp.cl[v] = static_cast<int32_t>(mult);
+              mult *= 32;
+            }
+          }
+          break;
+        case HP_HW_CTA:
+          if (team_block) {
+            rp.cw[v] = static_cast<int32_t>(mult);
+            mult *= W;
+          }
+          break;
+        case HP_HW_CLUSTER:
+          if (team_block && rp.C > 1) {
+            rp.cr[v] = static_cast<int32_t>(mult);
+            mult *= rp.C;
+          }
+          break;
+        default:
+          break;
+      }
+    }
+    if (mult > (int64_t(1) << 30)) return bad("too many parallel slots on one level");
+    rp.vP[v] = static_cast<int32_t>(mult);
+    rp.vn[v] = vls[v].n;
+    rp.vstride[v] = vls[v].stride;
+  }
+  // team lanes: the number of lanes inside one team
+  if (rp.team == TEAM_LANES) {
+    if (T == HP_HW_SUBWARP) rp.grp_lanes = rp.L;     // no finer groups inside a sub-warp team
+    if (T >= HP_HW_LANE) rp.grp_lanes = 1;
+  }
+  int64_t items;
+  if (__builtin_mul_overflow(O, static_cast<int64_t>(rp.G), &items)) return bad("too many work items");
+  rp.items = items;
+  rp.M = 1;
+  p.kernel = team_block ? (rp.C > 1 ? "rect_block_cluster" : "rect_block") : "rect_lanes";
+  *out = p;
+  return HP_OK;
+}
+
+std::string describe_plan(const NestPlan& p) {
+  std::ostringstream s;
+  const RectPlan& rp = p.rp;
+  s << "{\"kind\":\"rect\",\"depth\":" << p.depth << ",\"red_level\":" << p.red_level << ",\"extents\":[";
+  for (int l = 0; l < p.depth; ++l) s << (l ? "," : "") << p.ext[l];
+  s << "],\"map\":[";
+  for (int l = 0; l < p.depth; ++l)
+    s << (l ? "," : "") << "{\"hw\":\"" << hw_name(p.map[l].hw) << "\",\"sub_width\":" << p.map[l].sub_width
+      << ",\"tile\":" << p.map[l].tile << "}";
+  s << "],\"auto_map\":" << (p.auto_map ? "true" : "false") << ",\"team\":\"" << team_name(rp.team)
+    << "\",\"outputs\":" << rp.O << ",\"reduced\":" << rp.R << ",\"items\":" << rp.items
+    << ",\"cluster\":" << rp.C << ",\"warps\":" << rp.W << ",\"team_lanes\":" << rp.L
+    << ",\"group_lanes\":" << rp.grp_lanes << ",\"vec\":" << rp.V << ",\"grid_parts\":" << rp.G
+    << ",\"tile\":" << rp.tile << ",\"levels\":[";
+  for (int v = 0; v < rp.nv; ++v)
+    s << (v ? "," : "") << "{\"n\":" << rp.vn[v] << ",\"stride\":" << rp.vstride[v] << ",\"slots\":" << rp.vP[v]
+      << ",\"c_rank\":" << rp.cr[v] << ",\"c_warp\":" << rp.cw[v] << ",\"c_group\":" << rp.cg[v]
+      << ",\"c_lane\":" << rp.cl[v] << "}";
+  s << "],\"kernel\":\"" << p.kernel << "\"}";
+  return s.str();
+}
+
+}  // namespace hp
+
+namespace hp {
+
+// Normwise a-priori bound: |got - exact| <= bound * sum|t|.
+//   plain FP32: gamma_k with k = the longest chain of roundings one term goes
+//   through (its thread's sequential share, the vector fold, the lane
+//   butterfly, the warp / rank / grid-part folds);
+//   compensated FP32 (Dot2): u + gamma_k^2, plus the FP64 grid combine.
+double error_bound_rect(const NestPlan& p) {
+  const RectPlan& rp = p.rp;
+  if (p.prec == HP_I32 || p.prec == HP_I64 || p.op != HP_RED_SUM || rp.team == TEAM_MAP) return 0.0;
+  const double u = std::ldexp(1.0, -24);
+  int64_t seq = 1;
+  for (int v = 0; v < rp.nv; ++v) {
+    int64_t n = rp.vn[v];
+    if (rp.split && v == 0) n = rp.tile;
+    seq *= (n + rp.vP[v] - 1) / std::max<int64_t>(rp.vP[v], 1);
+  }
+  int64_t k = seq + 2 /*vector*/ + 5 /*butterfly*/;
+  if (rp.team == TEAM_BLOCK) k += rp.W + rp.C;
+  if (p.prec == HP_F32) k += rp.G;
+  const double g = (k * u) / (1.0 - k * u);
+  if (p.prec == HP_F32) return g;
+  return u + g * g + static_cast<double>(rp.G) * std::ldexp(1.0, -52);
+}
+
+}  // namespace hp

@@ -1,0 +1,296 @@
+// rect_kernels.cuh — the rectangular nest executor (device code).
+//
+// One output of the nest is combined by a team (plan.cpp decides which):
+//   rect_block_kernel  a cluster of C CTAs or a single CTA.  Each thread folds
+//                      its share of the reduced levels, then lanes combine by
+//                      xor-shuffle (Sec. 3.7), warps through shared memory in
+//                      warp order (Sec. 3.7's fallback one level up), CTAs of
+//                      a cluster through distributed shared memory in rank
+//                      order; items are handled in rounds of M so that one
+//                      barrier serves M outputs.
+//   rect_lanes_kernel  a group of L lanes of one warp (warp, sub-warp group of
+//                      Sec. 3.8, or a single thread): lanes combine by
+//                      xor-shuffle with width L.
+// When the first reduced level is bound to the grid, every output is cut into
+// G parts that write partials; rect_combine_kernel folds them in part order
+// (FP64 for compensated sums).  The reduction tree depends only on the plan,
+// never on which SM ran what, so runs are bit-reproducible.
+#pragma once
+
+#include <cooperative_groups.h>
+#include <cstdint>
+
+#include "accum.cuh"
+#include "hp_internal.h"
+
+namespace hp {
+
+namespace cg = cooperative_groups;
+
+// ---------------------------------------------------------------- loads
+__device__ __forceinline__ float4 ld_stream4(const float* p) { return __ldcs(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ int4 ld_stream4(const int32_t* p) { return __ldcs(reinterpret_cast<const int4*>(p)); }
+__device__ __forceinline__ float4 ld_keep4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ int4 ld_keep4(const int32_t* p) { return __ldg(reinterpret_cast<const int4*>(p)); }
+__device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
+__device__ __forceinline__ int32_t ld_stream(const int32_t* p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_keep(const float* p) { return __ldg(p); }
+__device__ __forceinline__ int32_t ld_keep(const int32_t* p) { return __ldg(p); }
+
+template <class V4>
+__device__ __forceinline__ auto v4get(const V4& v, int i) {
+  return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+
+// ---------------------------------------------------------------- bodies
+// fold V consecutive iterations starting at flat (reduced index rflat)
+template <class Op>
+struct BodyLoad {
+  const typename Op::In* A;
+  template <int V>
+  __device__ __forceinline__ void fold(typename Op::Acc (&acc)[V], int64_t flat, int64_t) const {
+    if constexpr (V == 4) {
+      const auto a = ld_stream4(A + flat);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) Op::add_val(acc[i], v4get(a, i));
+    } else {
+#pragma unroll
+      for (int i = 0; i < V; ++i) Op::add_val(acc[i], ld_stream(A + flat + i));
+    }
+  }
+};
+
+template <class Op>
+struct BodyDot {
+  const typename Op::In* A;
+  const typename Op::In* w;
+  template <int V>
+  __device__ __forceinline__ void fold(typename Op::Acc (&acc)[V], int64_t flat, int64_t rflat) const {
+    if constexpr (V == 4) {
+      const auto a = ld_stream4(A + flat);
+      const auto b = ld_keep4(w + rflat);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) Op::add_prod(acc[i], v4get(a, i), v4get(b, i));
+    } else {
+#pragma unroll
+      for (int i = 0; i < V; ++i) Op::add_prod(acc[i], ld_stream(A + flat + i), ld_keep(w + rflat + i));
+    }
+  }
+};
+
+// a + b * (flat mod m): exact in int64, wrapped for int32, rounded once for FP
+template <class Op>
+struct BodyAffine {
+  int64_t a, b, m;
+  template <int V>
+  __device__ __forceinline__ void fold(typename Op::Acc (&acc)[V], int64_t flat, int64_t) const {
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+      const int64_t v = a + b * ((flat + i) % m);
+      if constexpr (Op::kFp) {
+        Op::add_val(acc[i], static_cast<float>(v));
+      } else if constexpr (sizeof(typename Op::Out) == 4) {
+        Op::add_val(acc[i], static_cast<int32_t>(static_cast<uint32_t>(static_cast<uint64_t>(v))));
+      } else {
+        Op::add_val(acc[i], static_cast<long long>(v));
+      }
+    }
+  }
+};
+
+// fl32(q^(flat mod m)) from a table the planner filled
+template <class Op>
+struct BodyGeo {
+  const float* table;
+  int64_t m;
+  template <int V>
+  __device__ __forceinline__ void fold(typename Op::Acc (&acc)[V], int64_t flat, int64_t) const {
+#pragma unroll
+    for (int i = 0; i < V; ++i) Op::add_val(acc[i], __ldg(table + (flat + i) % m));
+  }
+};
+
+// ---------------------------------------------------------------- per-thread fold of one item
+template <class Op, int V, class Body>
+__device__ __forceinline__ void fold_item(const RectPlan& p, const Body& body, int64_t o, int64_t g,
+                                          const int32_t (&slot)[kMaxV], typename Op::Acc (&acc)[V]) {
+  const int nv = p.nv;
+  int64_t lo[kMaxV], hi[kMaxV], x[kMaxV];
+#pragma unroll
+  for (int v = 0; v < kMaxV; ++v) {
+    if (v < nv) {
+      lo[v] = 0;
+      hi[v] = p.vn[v];
+    }
+  }
+  if (p.split) {
+    lo[0] = g * p.tile;
+    hi[0] = (lo[0] + p.tile < p.vn[0]) ? lo[0] + p.tile : p.vn[0];
+  }
+  for (int v = 0; v < nv - 1; ++v) {
+    x[v] = lo[v] + slot[v];
+    if (x[v] >= hi[v]) return;
+  }
+  const int64_t obase = o * p.R;
+  const int last = nv - 1;
+  const int64_t in_lo = lo[last] + slot[last], in_hi = hi[last], P = p.vP[last];
+  while (true) {
+    int64_t roff = 0;
+    for (int v = 0; v < last; ++v) roff += x[v] * p.vstride[v];
+    const int64_t base = obase + roff;
+#pragma unroll 4
+    for (int64_t xi = in_lo; xi < in_hi; xi += P) body.template fold<V>(acc, base + xi, roff + xi);
+    int v = last - 1;
+    for (; v >= 0; --v) {
+      x[v] += p.vP[v];
+      if (x[v] < hi[v]) break;
+      x[v] = lo[v] + slot[v];
+    }
+    if (v < 0) break;
+  }
+}
+
+template <class Op, int V>
+__device__ __forceinline__ typename Op::Acc fold_vec(const typename Op::Acc (&acc)[V]) {
+  if constexpr (V == 4) return Op::combine(Op::combine(acc[0], acc[1]), Op::combine(acc[2], acc[3]));
+  else if constexpr (V == 2) return Op::combine(acc[0], acc[1]);
+  else return acc[0];
+}
+
+template <class Op>
+__device__ __forceinline__ typename Op::Acc lanes_allreduce(typename Op::Acc a, int width) {
+  for (int m = width >> 1; m >= 1; m >>= 1) a = Op::combine(a, Op::shfl_xor(a, m, width));
+  return a;
+}
+
+template <class Op>
+__device__ __forceinline__ void emit(const RectPlan& p, int64_t item, typename Op::Acc a, typename Op::Out* out,
+                                     typename Op::Acc* part) {
+  if (p.G == 1) out[item] = Op::finish(a);
+  else part[item] = a;
+}
+
+// ---------------------------------------------------------------- team = cluster or CTA
+template <class Op, int V, class Body>
+__global__ void __launch_bounds__(1024) rect_block_kernel(RectPlan p, Body body, typename Op::Out* out,
+                                                          typename Op::Acc* part) {
+  using Acc = typename Op::Acc;
+  __shared__ Acc wpart[2][kMaxM][kMaxWarps];
+  __shared__ Acc cpart[2][kMaxM];
+  const int C = p.C;
+  int rank = 0;
+  int64_t team = blockIdx.x, n_teams = gridDim.x;
+  if (C > 1) {
+    rank = static_cast<int>(cg::this_cluster().block_rank());
+    team = blockIdx.x / C;
+    n_teams = gridDim.x / C;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane / p.grp_lanes, lig = lane % p.grp_lanes;
+  int32_t slot[kMaxV];
+#pragma unroll
+  for (int v = 0; v < kMaxV; ++v)
+    slot[v] = rank * p.cr[v] + warp * p.cw[v] + grp * p.cg[v] + lig * p.cl[v];
+  const int M = p.M, W = p.W;
+  const int64_t n_chunks = (p.items + M - 1) / M;
+  int buf = 0;
+  for (int64_t chunk = team; chunk < n_chunks; chunk += n_teams) {
+    const int64_t item0 = chunk * M;
+    const int mcount = static_cast<int>((p.items - item0 < M) ? p.items - item0 : M);
+    for (int m = 0; m < mcount; ++m) {
+      const int64_t item = item0 + m;
+      const int64_t o = item / p.G, g = item - o * p.G;
+      Acc acc[V];
+#pragma unroll
+      for (int i = 0; i < V; ++i) acc[i] = Op::ident();
+      fold_item<Op, V>(p, body, o, g, slot, acc);
+      Acc a = lanes_allreduce<Op>(fold_vec<Op, V>(acc), 32);
+      if (lane == 0) wpart[buf][m][warp] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < mcount) {
+      Acc a = wpart[buf][threadIdx.x][0];
+      for (int w = 1; w < W; ++w) a = Op::combine(a, wpart[buf][threadIdx.x][w]);
+      cpart[buf][threadIdx.x] = a;
+    }
+    if (C > 1) {
+      cg::cluster_group cl = cg::this_cluster();
+      cl.sync();  // release own CTA partials, acquire the peers'
+      for (int m = rank + C * static_cast<int>(threadIdx.x); m < mcount; m += C * static_cast<int>(blockDim.x)) {
+        Acc a = *cl.map_shared_rank(&cpart[buf][m], 0);
+        for (int q = 1; q < C; ++q) a = Op::combine(a, *cl.map_shared_rank(&cpart[buf][m], q));
+        emit<Op>(p, item0 + m, a, out, part);
+      }
+    } else if (threadIdx.x < mcount) {
+      emit<Op>(p, item0 + threadIdx.x, cpart[buf][threadIdx.x], out, part);
+    }
+    buf ^= 1;
+  }
+  if (C > 1) cg::this_cluster().sync();  // peers may still read this CTA's partials
+}
+
+// ---------------------------------------------------------------- team = L lanes of a warp
+template <class Op, int V, class Body>
+__global__ void __launch_bounds__(1024) rect_lanes_kernel(RectPlan p, Body body, typename Op::Out* out,
+                                                          typename Op::Acc* part) {
+  using Acc = typename Op::Acc;
+  const int L = p.L;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lt = lane % L;
+  const int grp = lt / p.grp_lanes, lig = lt % p.grp_lanes;
+  int32_t slot[kMaxV];
+#pragma unroll
+  for (int v = 0; v < kMaxV; ++v) slot[v] = grp * p.cg[v] + lig * p.cl[v];
+  const int teams_per_warp = 32 / L;
+  const int64_t warp_global = static_cast<int64_t>(blockIdx.x) * p.W + warp;
+  const int64_t n_teams = static_cast<int64_t>(gridDim.x) * p.W * teams_per_warp;
+  for (int64_t base = warp_global * teams_per_warp; base < p.items; base += n_teams) {
+    const int64_t item = base + lane / L;
+    const bool valid = item < p.items;
+    Acc acc[V];
+#pragma unroll
+    for (int i = 0; i < V; ++i) acc[i] = Op::ident();
+    if (valid) {
+      const int64_t o = item / p.G, g = item - o * p.G;
+      fold_item<Op, V>(p, body, o, g, slot, acc);
+    }
+    Acc a = lanes_allreduce<Op>(fold_vec<Op, V>(acc), L);
+    if (valid && lt == 0) emit<Op>(p, item, a, out, part);
+  }
+}
+
+// ---------------------------------------------------------------- grid parts -> outputs
+template <class Op>
+__global__ void rect_combine_kernel(int64_t O, int32_t G, const typename Op::Acc* part, typename Op::Out* out) {
+  for (int64_t o = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; o < O;
+       o += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const typename Op::Acc* pp = part + o * G;
+    if constexpr (sizeof(typename Op::Acc) == 8 && Op::kFp) {
+      // compensated FP32 partials: the final grid-level combine runs in FP64
+      double s = 0.0;
+      for (int g = 0; g < G; ++g) {
+        const f2 v = *reinterpret_cast<const f2*>(pp + g);
+        s += static_cast<double>(v.s);
+        s += static_cast<double>(v.c);
+      }
+      out[o] = static_cast<float>(s);
+    } else {
+      typename Op::Acc a = pp[0];
+      for (int g = 1; g < G; ++g) a = Op::combine(a, pp[g]);
+      out[o] = Op::finish(a);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- no reduction: one output per iteration
+template <class Op, class Body>
+__global__ void rect_map_kernel(RectPlan p, Body body, typename Op::Out* out) {
+  for (int64_t f = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; f < p.O;
+       f += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    typename Op::Acc acc[1] = {Op::ident()};
+    body.template fold<1>(acc, f, 0);
+    out[f] = Op::finish(acc[0]);
+  }
+}
+
+}  // namespace hp
