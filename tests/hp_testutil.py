@@ -2,7 +2,9 @@
 compare with the oracle.
 
 Tolerances (the paper fixes none; these are the readings the design states):
-  * integer precisions and MAX / MIN: bit-exact;
+  * integer precisions and MAX / MIN: bit-exact (FP max / min against the
+    oracle's exact value rounded to FP32, which rounding's monotonicity makes
+    the max / min of the FP32 body values);
   * compensated FP32 sums: |got - ref| <= 1e-6 * max(|ref|, 2^-20 * sum|t|);
   * plain FP32 sums:       |got - ref| <= 1e-5 * max(|ref|, sqrt(sum t^2));
   * both also within the library's own a-priori bound:
@@ -86,6 +88,9 @@ def assert_close(got, ref: "oracle.Result", prec: str, op: str, bound: float | N
     g = got.astype(np.float64)
     r = ref.values
     if op in ("max", "min"):
+        # the body value is an FP32 number; rounding to FP32 is monotonic, so the
+        # max / min of the rounded values is the oracle's exact max / min rounded
+        r = r.astype(np.float32).astype(np.float64)
         bad = np.nonzero(g != r)[0]
         assert bad.size == 0, f"{what}: {bad.size} max/min mismatches at {bad[:5]}: got {g[bad[:5]]} want {r[bad[:5]]}"
         return 0.0
