@@ -247,6 +247,17 @@ hp_status hp_serve_stats(const hp_server *s, double *p50_us, double *p99_us, dou
 
 void hp_serve_destroy(hp_server *s);
 
+/*
+ * Process-wide planner options, read when a nest is created (existing nests
+ * keep their plan).  Names:
+ *   "pipeline"  1 (default): block teams whose element groups allow it stream
+ *               their inputs through per-thread cp.async rings; 0: plain loads.
+ *               Both give bit-identical results (same reduction tree).
+ * HP_EINVAL for an unknown name.
+ */
+hp_status hp_set_option(const char *name, int64_t value);
+hp_status hp_get_option(const char *name, int64_t *value);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *hp_last_error(void);
 

@@ -38,7 +38,8 @@ BODIES = {"load": HP_BODY_LOAD, "dot_bcast": HP_BODY_DOT_BCAST, "csr_gather": HP
 # every entry point include/hp.h declares
 EXPORTED = ["hp_nest_create", "hp_nest_run", "hp_nest_run_host", "hp_nest_run_batch", "hp_nest_error_bound",
             "hp_nest_describe", "hp_nest_check", "hp_nest_destroy", "hp_serve_create", "hp_serve_submit",
-            "hp_serve_poll", "hp_serve_stats", "hp_serve_destroy", "hp_last_error", "hp_version"]
+            "hp_serve_poll", "hp_serve_stats", "hp_serve_destroy", "hp_set_option", "hp_get_option",
+            "hp_last_error", "hp_version"]
 
 
 class hp_level_map(ctypes.Structure):
@@ -110,6 +111,10 @@ def lib() -> ctypes.CDLL:
         L.hp_last_error.argtypes = []
         L.hp_version.restype = i32
         L.hp_version.argtypes = []
+        L.hp_set_option.restype = i32
+        L.hp_set_option.argtypes = [ctypes.c_char_p, i64]
+        L.hp_get_option.restype = i32
+        L.hp_get_option.argtypes = [ctypes.c_char_p, ctypes.POINTER(i64)]
         _lib = L
         return L
 
@@ -120,6 +125,16 @@ def hp_last_error() -> str:
 
 def hp_version() -> int:
     return lib().hp_version()
+
+
+def hp_set_option(name: str, value: int):
+    _check(lib().hp_set_option(name.encode(), int(value)), "hp_set_option")
+
+
+def hp_get_option(name: str) -> int:
+    v = ctypes.c_int64()
+    _check(lib().hp_get_option(name.encode(), ctypes.byref(v)), "hp_get_option")
+    return v.value
 
 
 def _check(st: int, where: str):

@@ -100,6 +100,26 @@ extern "C" {
 
 int hp_version(void) { return 100; }
 
+hp_status hp_set_option(const char* name, int64_t value) {
+  if (!name) return fail(HP_EINVAL, "option name is NULL");
+  const std::string n(name);
+  if (n == "pipeline") {
+    options().pipeline = value;
+    return HP_OK;
+  }
+  return fail(HP_EINVAL, "unknown option " + n);
+}
+
+hp_status hp_get_option(const char* name, int64_t* value) {
+  if (!name || !value) return fail(HP_EINVAL, "NULL argument");
+  const std::string n(name);
+  if (n == "pipeline") {
+    *value = options().pipeline;
+    return HP_OK;
+  }
+  return fail(HP_EINVAL, "unknown option " + n);
+}
+
 const char* hp_last_error(void) { return last_error_string().c_str(); }
 
 hp_status hp_nest_create(int depth, const int64_t* extents, const int64_t* csr_offsets, int64_t n_rows,

@@ -16,6 +16,7 @@ constexpr int kMaxV = HP_MAX_DEPTH;  // reduced virtual levels
 constexpr int kMaxM = 32;            // items per synchronisation round of a block team
 constexpr int kMaxWarps = 32;
 constexpr int kGeoMax = 1024;        // GEOMETRIC table entries
+constexpr int kPipeGroupsMax = 8;    // element groups per thread per item of the pipelined kernel
 
 // Hardware scopes, coarse to fine (same order and values as hp_hw).
 enum Scope : int32_t { S_GRID = 0, S_CLUSTER = 1, S_CTA = 2, S_WARP = 3, S_SUB = 4, S_LANE = 5, S_SEQ = 6 };
@@ -49,6 +50,8 @@ struct RectPlan {
   int32_t G;               // grid parts per output
   int32_t M;               // items per round (TEAM_BLOCK)
   int32_t body;            // hp_body
+  int32_t pipe;            // 1: TEAM_BLOCK runs the cp.async-pipelined kernel
+  int32_t groups;          // element groups per thread per item (max over threads)
   int32_t geo_m;
   int64_t aff_a, aff_b, aff_m;
 };
@@ -103,6 +106,12 @@ std::string describe_plan(const NestPlan& p);
 
 // A-priori bound on |got - exact| / sum|t| for one FP result of the plan.
 double error_bound_rect(const NestPlan& p);
+
+// Process-wide options read when a nest is planned (hp_set_option).
+struct Options {
+  int64_t pipeline = 1;    // allow the cp.async-pipelined block kernel
+};
+Options& options();
 
 // Thread-local last-error message.
 void set_error(const std::string& msg);

@@ -44,6 +44,11 @@ bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 constexpr int64_t kAssumedSMs = 152;
 }  // namespace
 
+Options& options() {
+  static Options o;
+  return o;
+}
+
 void set_error(const std::string& msg) { g_last_error = msg; }
 hp_status fail(hp_status st, const std::string& msg) {
   g_last_error = msg;
@@ -373,7 +378,22 @@ hp_status plan_rect(int depth, const int64_t* extents, const hp_level_map* map, 
   if (__builtin_mul_overflow(O, static_cast<int64_t>(rp.G), &items)) return bad("too many work items");
   rp.items = items;
   rp.M = 1;
-  p.kernel = team_block ? (rp.C > 1 ? "rect_block_cluster" : "rect_block") : "rect_lanes";
+  // element groups per thread per item: the thread with slot 0 on every level has the most
+  int64_t groups = 1;
+  for (int v = 0; v < nv; ++v) {
+    const int64_t n = (rp.split && v == 0) ? rp.tile : rp.vn[v];
+    groups *= (n + rp.vP[v] - 1) / rp.vP[v];
+    if (groups > (int64_t(1) << 30)) groups = int64_t(1) << 30;
+  }
+  rp.groups = static_cast<int32_t>(groups);
+  const bool mem_body = body == HP_BODY_LOAD || body == HP_BODY_DOT_BCAST;
+  rp.pipe = (options().pipeline != 0 && team_block && rp.V == 4 && mem_body && rp.G == 1 && rp.W <= 8 &&
+             R < (int64_t(1) << 31) && groups <= kPipeGroupsMax)
+                ? 1
+                : 0;
+  p.kernel = team_block ? (rp.pipe ? (rp.C > 1 ? "rect_block_pipe_cluster" : "rect_block_pipe")
+                                   : (rp.C > 1 ? "rect_block_cluster" : "rect_block"))
+                        : "rect_lanes";
   *out = p;
   return HP_OK;
 }
@@ -391,7 +411,7 @@ std::string describe_plan(const NestPlan& p) {
     << "\",\"outputs\":" << rp.O << ",\"reduced\":" << rp.R << ",\"items\":" << rp.items
     << ",\"cluster\":" << rp.C << ",\"warps\":" << rp.W << ",\"team_lanes\":" << rp.L
     << ",\"group_lanes\":" << rp.grp_lanes << ",\"vec\":" << rp.V << ",\"grid_parts\":" << rp.G
-    << ",\"tile\":" << rp.tile << ",\"levels\":[";
+    << ",\"tile\":" << rp.tile << ",\"groups\":" << rp.groups << ",\"pipe\":" << rp.pipe << ",\"levels\":[";
   for (int v = 0; v < rp.nv; ++v)
     s << (v ? "," : "") << "{\"n\":" << rp.vn[v] << ",\"stride\":" << rp.vstride[v] << ",\"slots\":" << rp.vP[v]
       << ",\"c_rank\":" << rp.cr[v] << ",\"c_warp\":" << rp.cw[v] << ",\"c_group\":" << rp.cg[v]

@@ -46,7 +46,10 @@ __device__ __forceinline__ auto v4get(const V4& v, int i) {
 // fold V consecutive iterations starting at flat (reduced index rflat)
 template <class Op>
 struct BodyLoad {
+  static constexpr bool kPipeable = true;
+  static constexpr bool kDot = false;
   const typename Op::In* A;
+  __host__ __device__ const typename Op::In* wptr() const { return nullptr; }
   template <int V>
   __device__ __forceinline__ void fold(typename Op::Acc (&acc)[V], int64_t flat, int64_t) const {
     if constexpr (V == 4) {
@@ -62,8 +65,11 @@ struct BodyLoad {
 
 template <class Op>
 struct BodyDot {
+  static constexpr bool kPipeable = true;
+  static constexpr bool kDot = true;
   const typename Op::In* A;
   const typename Op::In* w;
+  __host__ __device__ const typename Op::In* wptr() const { return w; }
   template <int V>
   __device__ __forceinline__ void fold(typename Op::Acc (&acc)[V], int64_t flat, int64_t rflat) const {
     if constexpr (V == 4) {
@@ -81,6 +87,10 @@ struct BodyDot {
 // a + b * (flat mod m): exact in int64, wrapped for int32, rounded once for FP
 template <class Op>
 struct BodyAffine {
+  static constexpr bool kPipeable = false;
+  static constexpr bool kDot = false;
+  const typename Op::In* A = nullptr;
+  __host__ __device__ const typename Op::In* wptr() const { return nullptr; }
   int64_t a, b, m;
   template <int V>
   __device__ __forceinline__ void fold(typename Op::Acc (&acc)[V], int64_t flat, int64_t) const {
@@ -101,6 +111,10 @@ struct BodyAffine {
 // fl32(q^(flat mod m)) from a table the planner filled
 template <class Op>
 struct BodyGeo {
+  static constexpr bool kPipeable = false;
+  static constexpr bool kDot = false;
+  const typename Op::In* A = nullptr;
+  __host__ __device__ const typename Op::In* wptr() const { return nullptr; }
   const float* table;
   int64_t m;
   template <int V>
@@ -228,6 +242,203 @@ __global__ void __launch_bounds__(1024) rect_block_kernel(RectPlan p, Body body,
   }
   if (C > 1) cg::this_cluster().sync();  // peers may still read this CTA's partials
 }
+
+// ---------------------------------------------------------------- team = cluster or CTA, pipelined
+// Same plan, same fold order and reduction tree as rect_block_kernel (results
+// are bit-identical), but every thread streams its own 128-bit element groups
+// through a private ring of D item stages in shared memory filled by cp.async,
+// so D items' loads per thread stay in flight across item boundaries and
+// across the CTA / cluster barriers of the rounds.  A thread only ever reads
+// the slots it filled itself, so the ring needs no barrier: cp.async.wait_group
+// orders each read after its own copies, and a stage is refilled only after
+// the values read from it have been consumed by the folds.
+constexpr int kPatMax = 8;    // element groups per thread per item
+constexpr int kPipeMaxThreads = 256;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <class In> struct Vec4Of;
+template <> struct Vec4Of<float> { using T = float4; };
+template <> struct Vec4Of<int32_t> { using T = int4; };
+
+template <class Op, class V4>
+__device__ __forceinline__ void fold4_load(typename Op::Acc (&acc)[4], const V4& a) {
+  Op::add_val(acc[0], a.x);
+  Op::add_val(acc[1], a.y);
+  Op::add_val(acc[2], a.z);
+  Op::add_val(acc[3], a.w);
+}
+template <class Op, class V4>
+__device__ __forceinline__ void fold4_dot(typename Op::Acc (&acc)[4], const V4& a, const V4& b) {
+  Op::add_prod(acc[0], a.x, b.x);
+  Op::add_prod(acc[1], a.y, b.y);
+  Op::add_prod(acc[2], a.z, b.z);
+  Op::add_prod(acc[3], a.w, b.w);
+}
+
+// the element groups (offsets within one output's reduced space) one thread
+// folds for any item, in fold_item's order; returns their number
+__device__ __forceinline__ int build_pattern(const RectPlan& p, const int32_t (&slot)[kMaxV], int32_t* pat,
+                                             int stride) {
+  const int nv = p.nv;
+  int64_t x[kMaxV];
+  int n = 0;
+  for (int v = 0; v < nv - 1; ++v) {
+    x[v] = slot[v];
+    if (x[v] >= p.vn[v]) return 0;
+  }
+  const int last = nv - 1;
+  while (true) {
+    int64_t roff = 0;
+    for (int v = 0; v < last; ++v) roff += x[v] * p.vstride[v];
+    for (int64_t xi = slot[last]; xi < p.vn[last]; xi += p.vP[last]) {
+      if (n < kPatMax) pat[n * stride] = static_cast<int32_t>(roff + xi);
+      ++n;
+    }
+    int v = last - 1;
+    for (; v >= 0; --v) {
+      x[v] += p.vP[v];
+      if (x[v] < p.vn[v]) break;
+      x[v] = slot[v];
+    }
+    if (v < 0) break;
+  }
+  return n < kPatMax ? n : kPatMax;  // the planner only picks this kernel when n <= kPatMax
+}
+
+// D items in flight per thread: each stage holds one item's element groups
+// (at most kPatMax 16-byte groups per thread), committed as one cp.async group.
+template <class Op, bool DOT, int D>
+__global__ void __launch_bounds__(kPipeMaxThreads, 3) rect_block_pipe_kernel(RectPlan p, const typename Op::In* __restrict__ A,
+                                                               const typename Op::In* __restrict__ w,
+                                                               typename Op::Out* out, typename Op::Acc* part) {
+  using Acc = typename Op::Acc;
+  using In = typename Op::In;
+  using V4 = typename Vec4Of<In>::T;
+  extern __shared__ __align__(16) unsigned char pipe_smem[];
+  const int nthr = blockDim.x, tid = threadIdx.x;
+  const int G = p.groups;                                            // stage width (groups per item)
+  V4* ring = reinterpret_cast<V4*>(pipe_smem);                      // [D][G][nthr]
+  int32_t* pat = reinterpret_cast<int32_t*>(pipe_smem);             // [kPatMax][nthr], before the ring is used
+  __shared__ Acc wpart[2][kMaxM][kPipeMaxThreads / 32];
+  __shared__ Acc cpart[2][kMaxM];
+  const int C = p.C;
+  int rank = 0;
+  int64_t team = blockIdx.x, n_teams = gridDim.x;
+  if (C > 1) {
+    rank = static_cast<int>(cg::this_cluster().block_rank());
+    team = blockIdx.x / C;
+    n_teams = gridDim.x / C;
+  }
+  const int warp = tid >> 5, lane = tid & 31;
+  const int grp = lane / p.grp_lanes, lig = lane % p.grp_lanes;
+  int32_t slot[kMaxV];
+#pragma unroll
+  for (int v = 0; v < kMaxV; ++v) slot[v] = rank * p.cr[v] + warp * p.cw[v] + grp * p.cg[v] + lig * p.cl[v];
+  const int nt = build_pattern(p, slot, pat + tid, nthr);
+  int32_t po[kPatMax];
+  V4 wv[kPatMax];
+#pragma unroll
+  for (int k = 0; k < kPatMax; ++k) {
+    po[k] = (k < nt) ? pat[k * nthr + tid] : 0;
+    if constexpr (DOT) {
+      if (k < nt) wv[k] = ld_keep4(w + po[k]);
+    }
+  }
+  __syncthreads();  // every pattern is in registers before the ring (same memory) fills
+  const int M = p.M, W = p.W;
+  const int64_t R = p.R, items = p.items;
+  const int64_t n_chunks = (items + M - 1) / M;
+  V4* const ring_t = ring + tid;
+  const int stage_stride = G * nthr;
+
+  // producer cursor over this team's items: item pm of chunk pc
+  int64_t pc = team;
+  int pm = 0;
+  int pcount = (pc < n_chunks) ? static_cast<int>((items - pc * M < M) ? items - pc * M : M) : 0;
+  bool pvalid = nt > 0 && pc < n_chunks;
+  const In* pitem = pvalid ? A + pc * M * R : A;
+  auto issue = [&](int stage) {
+    if (pvalid) {
+      V4* dst = ring_t + stage * stage_stride;
+#pragma unroll
+      for (int k = 0; k < kPatMax; ++k)
+        if (k < nt) cp_async16(dst + k * nthr, pitem + po[k]);
+      pitem += R;
+      if (++pm == pcount) {
+        pm = 0;
+        pc += n_teams;
+        pvalid = pc < n_chunks;
+        pcount = pvalid ? static_cast<int>((items - pc * M < M) ? items - pc * M : M) : 0;
+        if (pvalid) pitem = A + pc * M * R;
+      }
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int s = 0; s < D; ++s) issue(s);
+
+  int rstage = 0;
+  int buf = 0;
+  for (int64_t chunk = team; chunk < n_chunks; chunk += n_teams) {
+    const int64_t item0 = chunk * M;
+    const int mcount = static_cast<int>((items - item0 < M) ? items - item0 : M);
+    for (int m = 0; m < mcount; ++m) {
+      Acc acc[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[i] = Op::ident();
+      if (nt > 0) {
+        cp_async_wait<D - 1>();
+        const V4* src = ring_t + rstage * stage_stride;
+#pragma unroll
+        for (int k = 0; k < kPatMax; ++k) {
+          if (k < nt) {
+            const V4 a = src[k * nthr];
+            if constexpr (DOT) fold4_dot<Op>(acc, a, wv[k]);
+            else fold4_load<Op>(acc, a);
+          }
+        }
+        issue(rstage);   // the folds above consumed the stage
+        rstage = (rstage + 1 == D) ? 0 : rstage + 1;
+      }
+      Acc a = lanes_allreduce<Op>(fold_vec<Op, 4>(acc), 32);
+      if (lane == 0) wpart[buf][m][warp] = a;
+    }
+    __syncthreads();
+    if (tid < mcount) {
+      Acc a = wpart[buf][tid][0];
+      for (int q = 1; q < W; ++q) a = Op::combine(a, wpart[buf][tid][q]);
+      cpart[buf][tid] = a;
+    }
+    if (C > 1) {
+      cg::cluster_group cl = cg::this_cluster();
+      cl.sync();
+      for (int m = rank + C * tid; m < mcount; m += C * nthr) {
+        Acc a = *cl.map_shared_rank(&cpart[buf][m], 0);
+        for (int q = 1; q < C; ++q) a = Op::combine(a, *cl.map_shared_rank(&cpart[buf][m], q));
+        emit<Op>(p, item0 + m, a, out, part);
+      }
+    } else if (tid < mcount) {
+      emit<Op>(p, item0 + tid, cpart[buf][tid], out, part);
+    }
+    buf ^= 1;
+  }
+  cp_async_wait<0>();
+  if (C > 1) cg::this_cluster().sync();
+}
+
+// items in flight for a plan with G groups per item
+__host__ __device__ constexpr int pipe_depth(int groups) { return groups > 4 ? 2 : 4; }
 
 // ---------------------------------------------------------------- team = L lanes of a warp
 template <class Op, int V, class Body>

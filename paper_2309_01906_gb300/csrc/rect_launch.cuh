@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <string>
 
 #include "hp_internal.h"
@@ -43,14 +44,27 @@ hp_status launch_team(const NestPlan& np, RectPlan rp, LaunchCfg& cfg, const Bod
     return e == cudaSuccess ? HP_OK : cuda_fail(e, "rect_map_kernel launch");
   }
   const bool block = rp.team == TEAM_BLOCK;
+  constexpr bool kPipeable = Body::kPipeable && V == 4;
+  const bool pipe = kPipeable && block && rp.pipe;
   auto kb = rect_block_kernel<Op, V, Body>;
   auto kl = rect_lanes_kernel<Op, V, Body>;
-  const void* kfn = block ? reinterpret_cast<const void*>(kb) : reinterpret_cast<const void*>(kl);
+  const bool deep = rp.groups <= 4;
+  auto kp = deep ? rect_block_pipe_kernel<Op, Body::kDot, pipe_depth(4)> : rect_block_pipe_kernel<Op, Body::kDot, pipe_depth(8)>;
+  const void* kfn = pipe ? reinterpret_cast<const void*>(kp)
+                         : block ? reinterpret_cast<const void*>(kb) : reinterpret_cast<const void*>(kl);
+  const size_t dyn =
+      pipe ? static_cast<size_t>(32 * rp.W) *
+                 std::max<size_t>(pipe_depth(rp.groups) * rp.groups * 16, kPatMax * sizeof(int32_t))
+           : 0;
   if (!cfg.ready) {
     cfg.threads = 32 * rp.W;
     cfg.cluster = block ? rp.C : 1;
+    if (dyn > 0) {  // static + dynamic shared memory may exceed the 48 KiB default
+      e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
+      if (e != cudaSuccess) return cuda_fail(e, "dynamic shared memory size");
+    }
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, cfg.threads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, cfg.threads, dyn);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (per_sm < 1) return fail(HP_EUNSUPPORTED, "kernel does not fit on an SM with this CTA size");
     int64_t max_teams;
@@ -67,6 +81,7 @@ hp_status launch_team(const NestPlan& np, RectPlan rp, LaunchCfg& cfg, const Bod
       at[0].val.clusterDim.z = 1;
       lc.gridDim = dim3(rp.C * cfg.sms);
       lc.blockDim = dim3(cfg.threads);
+      lc.dynamicSmemBytes = dyn;
       lc.attrs = at;
       lc.numAttrs = 1;
       int n_clusters = 0;
@@ -114,8 +129,19 @@ hp_status launch_team(const NestPlan& np, RectPlan rp, LaunchCfg& cfg, const Bod
       lc.attrs = at;
       lc.numAttrs = 1;
     }
-    e = cudaLaunchKernelEx(&lc, kb, rp, body, out, part);
-    if (e != cudaSuccess) return cuda_fail(e, "rect_block_kernel launch");
+    if constexpr (kPipeable) {
+      if (pipe) {
+        lc.dynamicSmemBytes = dyn;
+        e = cudaLaunchKernelEx(&lc, kp, rp, body.A, body.wptr(), out, part);
+        if (e != cudaSuccess) return cuda_fail(e, "rect_block_pipe_kernel launch");
+      } else {
+        e = cudaLaunchKernelEx(&lc, kb, rp, body, out, part);
+        if (e != cudaSuccess) return cuda_fail(e, "rect_block_kernel launch");
+      }
+    } else {
+      e = cudaLaunchKernelEx(&lc, kb, rp, body, out, part);
+      if (e != cudaSuccess) return cuda_fail(e, "rect_block_kernel launch");
+    }
   } else {
     kl<<<cfg.grid, cfg.threads, 0, a.stream>>>(rp, body, out, part);
     e = cudaPeekAtLastError();
@@ -151,12 +177,17 @@ hp_status launch_rect(const NestPlan& np, LaunchCfg& cfg, const RectArgs& a) {
       return launch_v<Op>(np, rp, cfg, b, a);
     }
     case HP_BODY_AFFINE: {
-      BodyAffine<Op> b{rp.aff_a, rp.aff_b, rp.aff_m};
+      BodyAffine<Op> b;
+      b.a = rp.aff_a;
+      b.b = rp.aff_b;
+      b.m = rp.aff_m;
       return launch_v<Op>(np, rp, cfg, b, a);
     }
     case HP_BODY_GEOMETRIC: {
       if constexpr (Op::kFp && sizeof(typename Op::Out) == 4) {
-        BodyGeo<Op> b{a.geo, rp.geo_m};
+        BodyGeo<Op> b;
+        b.table = a.geo;
+        b.m = rp.geo_m;
         return launch_v<Op>(np, rp, cfg, b, a);
       }
       return fail(HP_EUNSUPPORTED, "GEOMETRIC body needs an FP precision");

@@ -74,7 +74,16 @@ def test_plan_four_level_cluster_map():
     # j over the 8 CTAs of the cluster (2 steps each); k over warps x lanes x 4 vector slots
     assert (j["n"], j["slots"], j["c_rank"], j["stride"]) == (16, 8, 1, 1024)
     assert (k["n"], k["slots"], k["c_warp"], k["c_lane"]) == (1024, 1024, 128, 4)
-    assert d["kernel"] == "rect_block_cluster"
+    assert d["kernel"] == "rect_block_pipe_cluster" and d["pipe"] == 1 and d["groups"] == 2
+    hb.hp_set_option("pipeline", 0)
+    try:
+        d = plan([64, 512, 16, 1024], 2, [("grid", 0, 0), ("grid", 0, 0), ("cluster", 8, 0), ("cta", 8, 0)])
+        assert d["kernel"] == "rect_block_cluster" and d["pipe"] == 0
+    finally:
+        hb.hp_set_option("pipeline", 1)
+    assert hb.hp_get_option("pipeline") == 1
+    with pytest.raises(hb.HPError):
+        hb.hp_set_option("no_such_option", 1)
 
 
 def test_plan_collapse_and_split():

@@ -143,6 +143,27 @@ def test_deterministic_and_map_invariant():
         assert all(np.array_equal(runs[0], r) for r in runs[1:]), f"not bit-reproducible under {m}"
 
 
+@pytest.mark.parametrize("prec", ["f32", "f32_comp", "i32", "i64"])
+def test_pipelined_equals_plain_loads(prec):
+    # the cp.async-pipelined block kernel folds in the same order: bit-identical
+    from paper_2309_01906_gb300 import binding as hb
+    for ext, r, lm in (([3, 7, 16, 132], 2, [("grid", 0, 0), ("grid", 0, 0), ("cluster", 8, 0), ("cta", 8, 0)]),
+                       ([40, 1028], 1, ["grid", ("cta", 4, 0)]),
+                       ([3, 5, 16, 512], 2, [("grid", 0, 0), ("grid", 0, 0), ("cluster", 4, 0), ("cta", 2, 0)])):
+        A, w = _inputs(ext, r, prec, "dot_bcast")
+        got = {}
+        for pipe in (1, 0):
+            hb.hp_set_option("pipeline", pipe)
+            try:
+                got[pipe], plan, bound = gpu_rect(ext, r, "sum", prec, "dot_bcast", lm, A=A, w=w)
+            finally:
+                hb.hp_set_option("pipeline", 1)
+            assert plan["pipe"] == pipe
+        assert np.array_equal(got[0], got[1]), (ext, lm)
+        ref = oracle_rect(ext, r, "sum", prec, "dot_bcast", A=A, w=w)
+        assert_close(got[1], ref, prec, "sum", bound, what=f"pipelined {ext}")
+
+
 def test_paper_simd8_example():
     # Sec. 3.6: 32 values, parallel level(simd(8)): 8 lanes, each sums 4 values
     A = np.arange(1, 33, dtype=np.int32)
