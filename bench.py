@@ -2,9 +2,10 @@
 
 Workload: the 4-level rectangular nest b=64 x i=512 x j=16 x k=1024,
 out[b][i] = sum_j sum_k A[b][i][j][k] * w[j][k], A FP32 normal(0, 1) (2 GiB),
-w FP32 uniform[-1, 1]; levels bound grid / grid / cluster (8 CTAs) / CTA
-(8 warps): k reduced by lanes (xor-shuffle) and warps (shared memory), j by the
-CTAs of a cluster (distributed shared memory).  Compensated FP32 accumulation.
+w FP32 uniform[-1, 1]; levels bound grid / grid / cluster (4 CTAs) / CTA
+(4 warps): k reduced by lanes (xor-shuffle) and warps (shared memory), j by the
+CTAs of a cluster (distributed shared memory), each CTA folding 4 of the 16 j
+rows.  Compensated FP32 accumulation.
 
 One step = one run of the nest (all its launches) over the resident inputs.
 Metric: nest iterations per second (2^29 iterations per step).
@@ -34,7 +35,7 @@ if ROOT not in sys.path:
 
 EXTENTS = [64, 512, 16, 1024]
 RED_LEVEL = 2
-LEVEL_MAP = [("grid", 0, 0), ("grid", 0, 0), ("cluster", 8, 0), ("cta", 8, 0)]
+LEVEL_MAP = [("grid", 0, 0), ("grid", 0, 0), ("cluster", 4, 0), ("cta", 4, 0)]
 ITERS = int(np.prod(EXTENTS))
 N_OUT = EXTENTS[0] * EXTENTS[1]
 R = EXTENTS[2] * EXTENTS[3]
@@ -220,7 +221,7 @@ def run_hp(args):
             "data": "synthetic (seeded): A normal(0,1) seed 3, w uniform[-1,1] seed 4",
             "config": {
                 "workload": WORKLOAD,
-                "map": "b,i->grid; j->cluster(8 CTAs, DSMEM); k->CTA(8 warps x 32 lanes x 4 vector slots)",
+                "map": "b,i->grid; j->cluster(4 CTAs, DSMEM); k->CTA(4 warps x 32 lanes x 4 vector slots)",
                 "precision": "compensated FP32 (Dot2) at every level",
                 "l2": "inputs (2 GiB) larger than L2 (129 MB); no flush",
                 "plan": {k: plan[k] for k in ("team", "cluster", "warps", "vec", "grid_parts", "kernel")},

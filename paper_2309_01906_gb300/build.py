@@ -1,7 +1,8 @@
 """Build libhp.so (the C-ABI library) in-tree for sm_103a.
 
 Every translation unit under csrc/ is compiled by nvcc in parallel, then linked
-with the static CUDA runtime into ``paper_2309_01906_gb300/libhp.so``.  No GPU
+with the static CUDA runtime into ``paper_2309_01906_gb300/libhp.so``.
+Extra nvcc flags may be given in the environment variable HP_NVCC_EXTRA.  No GPU
 is needed to build (nvcc cross-compiles).  Object files go to ``_build/`` at the
 repository root.
 """
@@ -43,7 +44,7 @@ def _deps_mtime() -> float:
 
 
 def up_to_date() -> bool:
-    return os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime()
+    return os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime() and not os.environ.get("HP_NVCC_EXTRA")
 
 
 def build(verbose: bool = False, force: bool = False, ptxas_verbose: bool = False) -> str:
@@ -52,6 +53,7 @@ def build(verbose: bool = False, force: bool = False, ptxas_verbose: bool = Fals
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_verbose else []
+    extra += os.environ.get("HP_NVCC_EXTRA", "").split()
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")

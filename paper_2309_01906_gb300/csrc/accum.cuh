@@ -192,4 +192,124 @@ struct OpI64Min {
   __device__ static Out finish(Acc a) { return a; }
 };
 
+// ---------------------------------------------------------------------------
+// Packed FP32x2 arithmetic (PTX add/sub/mul/fma .rn.f32x2, sm_100 and later):
+// each half is an IEEE round-to-nearest FP32 operation, so a pair of
+// independent accumulators advanced by one packed instruction gives exactly
+// the results of two scalar instructions.
+#define HP_F32X2_OP2(name, op)                                                                   \
+  __device__ __forceinline__ float2 name(float2 a, float2 b) {                                    \
+    float2 r;                                                                                    \
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n " op     \
+        " rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"                                              \
+        : "=f"(r.x), "=f"(r.y)                                                                   \
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));                                               \
+    return r;                                                                                    \
+  }
+HP_F32X2_OP2(add2, "add.rn.f32x2")
+HP_F32X2_OP2(sub2, "sub.rn.f32x2")
+HP_F32X2_OP2(mul2, "mul.rn.f32x2")
+#undef HP_F32X2_OP2
+
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  float2 r;
+  asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+      " mov.b64 rc, {%6, %7};\n fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return r;
+}
+
+// TwoSum on two lanes at once
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  s = add2(a, b);
+  const float2 bb = sub2(s, a);
+  e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+
+// Fold state of the 4 vector slots of one thread.  The generic version uses
+// the policy's scalar operations; FP32 sums use packed pairs (slots 0,1 and
+// 2,3) with the same per-slot operation sequence, hence identical results.
+template <class Op>
+struct Fold4 {
+  typename Op::Acc a[4];
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = Op::ident();
+  }
+  template <class V4>
+  __device__ __forceinline__ void load(const V4& x) {
+    Op::add_val(a[0], x.x);
+    Op::add_val(a[1], x.y);
+    Op::add_val(a[2], x.z);
+    Op::add_val(a[3], x.w);
+  }
+  template <class V4>
+  __device__ __forceinline__ void dot(const V4& x, const V4& w, const V4&) {
+    Op::add_prod(a[0], x.x, w.x);
+    Op::add_prod(a[1], x.y, w.y);
+    Op::add_prod(a[2], x.z, w.z);
+    Op::add_prod(a[3], x.w, w.w);
+  }
+  __device__ __forceinline__ void get(typename Op::Acc (&out)[4]) const {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) out[i] = a[i];
+  }
+};
+
+template <>
+struct Fold4<OpF32Comp> {
+  float2 s01, s23, c01, c23;   // leading and trailing words of slots (0,1) and (2,3)
+  __device__ __forceinline__ void init() { s01 = s23 = c01 = c23 = make_float2(0.0f, 0.0f); }
+  __device__ __forceinline__ void add_pair(float2& s, float2& c, float2 v) {
+    float2 t, e;
+    two_sum2(s, v, t, e);
+    s = t;
+    c = add2(c, e);
+  }
+  __device__ __forceinline__ void load(const float4& x) {
+    add_pair(s01, c01, make_float2(x.x, x.y));
+    add_pair(s23, c23, make_float2(x.z, x.w));
+  }
+  // the exact product errors come from two scalar FMAs (free operand negation)
+  __device__ __forceinline__ void prod_pair(float2& s, float2& c, float2 x, float2 w) {
+    const float2 p = mul2(x, w);
+    const float2 ep = make_float2(__fmaf_rn(x.x, w.x, -p.x), __fmaf_rn(x.y, w.y, -p.y));
+    float2 t, e;
+    two_sum2(s, p, t, e);
+    s = t;
+    c = add2(c, add2(ep, e));
+  }
+  __device__ __forceinline__ void dot(const float4& x, const float4& w, const float4&) {
+    prod_pair(s01, c01, make_float2(x.x, x.y), make_float2(w.x, w.y));
+    prod_pair(s23, c23, make_float2(x.z, x.w), make_float2(w.z, w.w));
+  }
+  __device__ __forceinline__ void get(f2 (&out)[4]) const {
+    out[0] = {s01.x, c01.x};
+    out[1] = {s01.y, c01.y};
+    out[2] = {s23.x, c23.x};
+    out[3] = {s23.y, c23.y};
+  }
+};
+
+template <>
+struct Fold4<OpF32Sum> {
+  float2 s01, s23;
+  __device__ __forceinline__ void init() { s01 = s23 = make_float2(0.0f, 0.0f); }
+  __device__ __forceinline__ void load(const float4& x) {
+    s01 = add2(s01, make_float2(x.x, x.y));
+    s23 = add2(s23, make_float2(x.z, x.w));
+  }
+  __device__ __forceinline__ void dot(const float4& x, const float4& w, const float4&) {
+    s01 = fma2(make_float2(x.x, x.y), make_float2(w.x, w.y), s01);
+    s23 = fma2(make_float2(x.z, x.w), make_float2(w.z, w.w), s23);
+  }
+  __device__ __forceinline__ void get(float (&out)[4]) const {
+    out[0] = s01.x;
+    out[1] = s01.y;
+    out[2] = s23.x;
+    out[3] = s23.y;
+  }
+};
+
 }  // namespace hp

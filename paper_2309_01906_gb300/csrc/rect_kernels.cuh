@@ -254,6 +254,9 @@ __global__ void __launch_bounds__(1024) rect_block_kernel(RectPlan p, Body body,
 // the values read from it have been consumed by the folds.
 constexpr int kPatMax = 8;    // element groups per thread per item
 constexpr int kPipeMaxThreads = 256;
+#ifndef HP_PIPE_MIN_BLOCKS
+#define HP_PIPE_MIN_BLOCKS 2   // resident CTAs per SM the register budget is sized for
+#endif
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -266,6 +269,9 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
+
+__device__ __forceinline__ float4 neg4(float4 v) { return make_float4(-v.x, -v.y, -v.z, -v.w); }
+__device__ __forceinline__ int4 neg4(int4 v) { return make_int4(-v.x, -v.y, -v.z, -v.w); }
 
 template <class In> struct Vec4Of;
 template <> struct Vec4Of<float> { using T = float4; };
@@ -319,7 +325,7 @@ __device__ __forceinline__ int build_pattern(const RectPlan& p, const int32_t (&
 // D items in flight per thread: each stage holds one item's element groups
 // (at most kPatMax 16-byte groups per thread), committed as one cp.async group.
 template <class Op, bool DOT, int D>
-__global__ void __launch_bounds__(kPipeMaxThreads, 3) rect_block_pipe_kernel(RectPlan p, const typename Op::In* __restrict__ A,
+__global__ void __launch_bounds__(kPipeMaxThreads, HP_PIPE_MIN_BLOCKS) rect_block_pipe_kernel(RectPlan p, const typename Op::In* __restrict__ A,
                                                                const typename Op::In* __restrict__ w,
                                                                typename Op::Out* out, typename Op::Acc* part) {
   using Acc = typename Op::Acc;
@@ -394,9 +400,8 @@ __global__ void __launch_bounds__(kPipeMaxThreads, 3) rect_block_pipe_kernel(Rec
     const int64_t item0 = chunk * M;
     const int mcount = static_cast<int>((items - item0 < M) ? items - item0 : M);
     for (int m = 0; m < mcount; ++m) {
-      Acc acc[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) acc[i] = Op::ident();
+      Fold4<Op> f;
+      f.init();
       if (nt > 0) {
         cp_async_wait<D - 1>();
         const V4* src = ring_t + rstage * stage_stride;
@@ -404,13 +409,15 @@ __global__ void __launch_bounds__(kPipeMaxThreads, 3) rect_block_pipe_kernel(Rec
         for (int k = 0; k < kPatMax; ++k) {
           if (k < nt) {
             const V4 a = src[k * nthr];
-            if constexpr (DOT) fold4_dot<Op>(acc, a, wv[k]);
-            else fold4_load<Op>(acc, a);
+            if constexpr (DOT) f.dot(a, wv[k], wv[k]);
+            else f.load(a);
           }
         }
         issue(rstage);   // the folds above consumed the stage
         rstage = (rstage + 1 == D) ? 0 : rstage + 1;
       }
+      Acc acc[4];
+      f.get(acc);
       Acc a = lanes_allreduce<Op>(fold_vec<Op, 4>(acc), 32);
       if (lane == 0) wpart[buf][m][warp] = a;
     }
