@@ -198,6 +198,26 @@ hp_status hp_nest_run(hp_nest *n, const void *const *in_dev, void *out_dev, void
 hp_status hp_nest_run_host(hp_nest *n, const void *const *in_host, void *out_host, void *stream);
 
 /*
+ * Run a rectangular nest without allocating any memory.  The paper has no
+ * counterpart to this entry point.  It is for callers that cannot allocate
+ * device memory at run time: latency-critical serving loops (cudaMalloc and
+ * cudaFree synchronise the whole device), services that handed out their
+ * whole device-memory budget at start-up, and code that runs while a
+ * framework holds its allocator.
+ *   Same kernels, same reduction tree and same results as hp_nest_run.  The
+ *   partials of a reduction split over grid parts live in one file-scope
+ *   device array of 8 MiB instead of per-nest scratch; every GPU that loads
+ *   the library holds that array until the process exits.  A plan that needs
+ *   more than 8 MiB of partials returns HP_EINVAL.
+ *   The first call on a device looks up the array's device address (with that
+ *   device current); make that first call before any stream capture.
+ *   All calls share the array and it keeps what the last call left: calls
+ *   whose work overlaps on the GPU (other streams or host threads) race.
+ *   CSR nests and the GEOMETRIC body (which needs a device table): HP_EUNSUPPORTED.
+ */
+hp_status hp_nest_run_static(hp_nest *n, const void *const *in_dev, void *out_dev, void *stream);
+
+/*
  * Run many independent nests in one persistent launch (replayed from a cached
  * CUDA graph).  nests[i], in_dev[i], out_dev[i] as for hp_nest_run.  All nests
  * must be rectangular.  Each nest's outputs equal those of hp_nest_run on the

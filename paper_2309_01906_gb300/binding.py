@@ -36,7 +36,8 @@ BODIES = {"load": HP_BODY_LOAD, "dot_bcast": HP_BODY_DOT_BCAST, "csr_gather": HP
           "affine": HP_BODY_AFFINE, "geometric": HP_BODY_GEOMETRIC}
 
 # every entry point include/hp.h declares
-EXPORTED = ["hp_nest_create", "hp_nest_run", "hp_nest_run_host", "hp_nest_run_batch", "hp_nest_error_bound",
+EXPORTED = ["hp_nest_create", "hp_nest_run", "hp_nest_run_host", "hp_nest_run_static", "hp_nest_run_batch",
+            "hp_nest_error_bound",
             "hp_nest_describe", "hp_nest_check", "hp_nest_destroy", "hp_serve_create", "hp_serve_submit",
             "hp_serve_poll", "hp_serve_stats", "hp_serve_destroy", "hp_set_option", "hp_get_option",
             "hp_last_error", "hp_version"]
@@ -87,6 +88,8 @@ def lib() -> ctypes.CDLL:
         L.hp_nest_run.argtypes = [p, p, p, p]
         L.hp_nest_run_host.restype = i32
         L.hp_nest_run_host.argtypes = [p, p, p, p]
+        L.hp_nest_run_static.restype = i32
+        L.hp_nest_run_static.argtypes = [p, p, p, p]
         L.hp_nest_run_batch.restype = i32
         L.hp_nest_run_batch.argtypes = [p, p, p, i32, p]
         L.hp_nest_error_bound.restype = i32
@@ -186,6 +189,12 @@ def hp_nest_run_host(nest, in_host_ptrs, out_host_ptr, stream=0):
     _check(st, "hp_nest_run_host")
 
 
+def hp_nest_run_static(nest, in_ptrs, out_ptr, stream=0):
+    """Run without allocating: grid-part partials go to the library's fixed static array."""
+    st = lib().hp_nest_run_static(nest, _ptr_array(in_ptrs), out_ptr or None, stream or None)
+    _check(st, "hp_nest_run_static")
+
+
 def hp_nest_run_batch(nests, in_ptr_lists, out_ptrs, stream=0):
     n = len(nests)
     harr = (ctypes.c_void_p * max(1, n))(*nests)
@@ -269,6 +278,9 @@ class Nest:
 
     def run(self, in_ptrs, out_ptr, stream=0):
         hp_nest_run(self.handle, in_ptrs, out_ptr, stream)
+
+    def run_static(self, in_ptrs, out_ptr, stream=0):
+        hp_nest_run_static(self.handle, in_ptrs, out_ptr, stream)
 
     def run_host(self, in_ptrs, out_ptr, stream=0):
         hp_nest_run_host(self.handle, in_ptrs, out_ptr, stream)
