@@ -42,6 +42,22 @@ R = EXTENTS[2] * EXTENTS[3]
 # algorithmic bytes of one launch: A once, w once, outputs once
 ALG_BYTES = ITERS * 4 + R * 4 + N_OUT * 4
 WORKLOAD = "4-level nest b=64 i=512 j=16 k=1024, out[b][i]=sum_j sum_k A[b][i][j][k]*w[j][k]"
+# DRAM traffic of one launch from an ncu capture (profiles/rect_block_pipe_4level_nest.md),
+# valid only while the kernel sources still hash to the fingerprint it was taken at
+TRAFFIC = {"sources": ["paper_2309_01906_gb300/csrc/rect_kernels.cuh", "paper_2309_01906_gb300/csrc/accum.cuh"],
+           "sha256_16": "59d53afe0cb3a553", "bytes_per_launch": 2194.6e6}
+
+
+def traffic_per_launch():
+    import hashlib
+    h = hashlib.sha256()
+    try:
+        for f in TRAFFIC["sources"]:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
+    except OSError:
+        return None
+    return TRAFFIC["bytes_per_launch"] if h.hexdigest()[:16] == TRAFFIC["sha256_16"] else None
 
 
 def measured_peaks():
@@ -233,7 +249,7 @@ def run_hp(args):
                 "peak": peak,
                 "unit": "GB/s",
                 "frac": achieved / peak,
-                "traffic": None,
+                "traffic": traffic_per_launch(),
                 "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": ALG_BYTES,
                 "kernel": plan["kernel"],
@@ -320,20 +336,54 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_profile_case(args):
+    """Reduced case for profiler captures: the headline nest with b = args.profile_b
+    (same map, same kernel), warm-up then `steps` runs, one timing line."""
+    import torch
+
+    from paper_2309_01906_gb300 import binding as hb
+    from paper_2309_01906_gb300 import synth
+    ext = [args.profile_b] + EXTENTS[1:]
+    A, w = synth.nest4_f32(*ext)
+    dA = torch.from_numpy(A.reshape(-1)).cuda()
+    dw = torch.from_numpy(w.reshape(-1)).cuda()
+    out = torch.empty(ext[0] * ext[1], dtype=torch.float32, device="cuda")
+    n = hb.Nest(ext, RED_LEVEL, "sum", args.prec, "dot_bcast", level_map=LEVEL_MAP)
+    sp = torch.cuda.current_stream().cuda_stream
+    for _ in range(args.warmup):
+        n.run([dA.data_ptr(), dw.data_ptr()], out.data_ptr(), sp)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        n.run([dA.data_ptr(), dw.data_ptr()], out.data_ptr(), sp)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"profile_case": ext, "prec": args.prec, "ms_per_launch": ms,
+                      "algorithmic_gbs": (A.nbytes + w.nbytes + out.numel() * 4) / ms / 1e6,
+                      "kernel": n.describe()["kernel"]}))
+    n.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="hp", choices=["hp", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-outputs", type=int, default=512)
+    ap.add_argument("--profile-b", type=int, default=0,
+                    help="profiler case: run only the headline nest with this outer extent b")
+    ap.add_argument("--prec", default="f32_comp", choices=["f32_comp", "f32"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile_b:
+        run_profile_case(args)
     else:
         run_hp(args)
 
