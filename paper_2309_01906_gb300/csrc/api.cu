@@ -228,7 +228,9 @@ hp_status hp_nest_check(hp_nest* n, void* stream, int32_t* device_error) {
   e = cudaMemcpy(&v, n->err, sizeof(v), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "read error word");
   if (device_error) *device_error = v;
-  if (v != 0) return fail(HP_ETIMEOUT, "a device-side bounded wait ran out (code " + std::to_string(v) + ")");
+  if (v != 0)
+    return fail(HP_ETIMEOUT, "device error word set (code " + std::to_string(v) +
+                                 (v == 2 ? ": CSR offsets or columns outside the declared sizes)" : ")"));
   return HP_OK;
 }
 

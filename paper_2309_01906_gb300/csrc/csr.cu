@@ -1,33 +1,87 @@
-// csr.cu — ragged (CSR) nests: planning and execution.
+// csr.cu — ragged (CSR) nests: out[i] = OP_{e in [off[i], off[i+1])} val[e] * x[col[e]]
+// and the count histogram hist[b] = #{e : col[e] >> shift == b}.
+//
+// The inner level is ragged, so its binding to hardware is chosen per row
+// (Sec. 3.3: a region compiled for several candidate levels, one picked at run
+// time; Sec. 3.8: sub-warp partitions for short rows).  Each run bins the rows
+// by length into classes and runs one kernel per class:
+//   class 0  len <= 4      one thread per row            (SEQ)
+//   class 1  len <= 32     a group of 8 lanes per row     (SUBWARP(8))
+//   class 2  len <= 1024   a warp per row                 (WARP)
+//   class 3  len <= 16384  a CTA of 256 threads per row   (CTA)
+//   class 4  longer        chunks of 16384 entries, a CTA per chunk; the CTA
+//                          that finishes a row's last chunk folds the chunk
+//                          partials in chunk order (GRID, two-pass; FP64 for
+//                          compensated sums), signalled by a per-row ticket
+//                          (atomic counter, no waiting).
+// Within a class, lane t of a row's team folds entries start + t + k*L (L the
+// team's lanes) into 4 accumulators (k mod 4), then the team combines them in
+// a fixed tree; the tree depends on the row's length only, never on which
+// team ran it or where the row sits in the class list, so results are
+// reproducible although the class lists are filled with atomics.
+// The histogram is counted in shared memory per CTA and flushed with 64-bit
+// integer atomics (exact in any order), fused into the same sweep or alone.
+// An explicit map for the entry level (SEQ, SUBWARP(w), WARP, CTA) puts every
+// row into that one class instead.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <new>
 #include <sstream>
 #include <string>
 
+#include "accum.cuh"
 #include "api_internal.h"
 
 namespace hp {
 
+constexpr int kCsrClasses = 5;
+constexpr int64_t kCsrLimit0 = 4, kCsrLimit1 = 32, kCsrLimit2 = 1024, kCsrLimit3 = 16384;  // class bounds (inclusive)
+constexpr int64_t kCsrChunk = 16384;                      // entries per chunk of a long row
+constexpr int kCsrCtaThreads = 256;
+constexpr int kCsrBinThreads = 256;
+constexpr int kCsrHistSmemMax = 12288;                   // bins counted in shared memory
+
 struct CsrState {
-  int dummy = 0;
+  int64_t* counters = nullptr;   // [0..4] rows per class, [5] chunk slots, [6..10] scatter cursors
+  int32_t* rows = nullptr;       // row ids grouped by class
+  int32_t* chunk_row = nullptr;  // per chunk slot: row id
+  int32_t* chunk_idx = nullptr;  // per chunk slot: chunk index within its row
+  int32_t* chunk_base = nullptr; // per chunk slot: first slot of its row
+  int32_t* chunk_cnt = nullptr;  // per chunk slot: chunks of its row
+  int32_t* tickets = nullptr;    // per chunk slot (only the row's first slot is used)
+  void* part = nullptr;          // per chunk slot: partial accumulator
+  int64_t max_chunks = 0;
+  int grid_rows = 0;             // persistent grid sizes
+  int grid_cta = 0;
 };
 
+// ---------------------------------------------------------------- planning
 hp_status plan_csr(int depth, int64_t n_rows, const hp_level_map* map, hp_red_op op, int red_level, hp_prec prec,
                    hp_body body, const void* body_params, CsrPlan* out, std::string* why) {
-  (void)map;
-  if (depth != 2) {
-    *why = "CSR nests have depth 2 (rows, entries)";
+  auto bad = [&](const std::string& s) {
+    *why = s;
     return HP_EINVAL;
-  }
-  if (n_rows < 0) {
-    *why = "n_rows must be >= 0";
-    return HP_EINVAL;
-  }
-  if (!body_params) {
-    *why = "CSR nests need hp_csr_params";
-    return HP_EINVAL;
-  }
+  };
+  if (depth != 2) return bad("CSR nests have depth 2 (rows, entries)");
+  if (n_rows < 0 || n_rows >= (int64_t(1) << 31)) return bad("CSR n_rows must be in [0, 2^31)");
+  if (!body_params) return bad("CSR nests need hp_csr_params");
   const hp_csr_params* cp = static_cast<const hp_csr_params*>(body_params);
+  if (cp->nnz < 0) return bad("CSR nnz must be >= 0");
+  if (cp->n_cols < 0 || cp->n_cols >= (int64_t(1) << 31)) return bad("CSR n_cols must be in [0, 2^31)");
+  if (op == HP_RED_HIST_COUNT || cp->fuse_hist) {
+    if (cp->n_bins < 1 || cp->n_bins >= (int64_t(1) << 31)) return bad("histogram n_bins must be in [1, 2^31)");
+    if (cp->hist_shift < 0 || cp->hist_shift > 30) return bad("histogram shift must be in [0, 30]");
+  }
+  if (op == HP_RED_HIST_COUNT) {
+    if (red_level != 0) return bad("a count histogram reduces over all levels (red_level 0)");
+    if (cp->fuse_hist) return bad("fuse_hist applies to SUM / MAX / MIN nests");
+  } else {
+    if (op != HP_RED_SUM && op != HP_RED_MAX && op != HP_RED_MIN) return bad("unknown reduction op");
+    if (red_level != 1) return bad("CSR nests reduce the entries of each row (red_level 1)");
+    if (body != HP_BODY_CSR_GATHER) return bad("CSR nests take the CSR_GATHER body");
+    if (prec != HP_F32 && prec != HP_F32_COMP) return bad("CSR nests compute in FP32 (plain or compensated)");
+  }
   CsrPlan p;
   p.n_rows = n_rows;
   p.nnz = cp->nnz;
@@ -37,35 +91,514 @@ hp_status plan_csr(int depth, int64_t n_rows, const hp_level_map* map, hp_red_op
   p.n_bins = cp->n_bins;
   p.op = op;
   p.prec = prec;
-  (void)red_level;
-  (void)body;
+  p.fixed_class = -1;
+  if (map) {
+    if (map[0].hw != HP_HW_GRID && map[0].hw != HP_HW_AUTO) return bad("CSR rows are bound to the grid");
+    const int hw = map[1].hw;
+    if (hw == HP_HW_AUTO) p.fixed_class = -1;
+    else if (hw == HP_HW_SEQ || hw == HP_HW_LANE) p.fixed_class = 0;
+    else if (hw == HP_HW_SUBWARP) {
+      if (map[1].sub_width != 8 && map[1].sub_width != 0) return bad("CSR sub-warp rows use groups of 8 lanes");
+      p.fixed_class = 1;
+    } else if (hw == HP_HW_WARP) p.fixed_class = 2;
+    else if (hw == HP_HW_CTA) p.fixed_class = 3;
+    else if (hw == HP_HW_GRID) p.fixed_class = 4;
+    else return bad("CSR entries bind to SEQ, SUBWARP(8), WARP, CTA, GRID or AUTO");
+  }
   *out = p;
   return HP_OK;
 }
 
 std::string describe_csr(const CsrPlan& p) {
   std::ostringstream s;
-  s << "{\"kind\":\"csr\",\"rows\":" << p.n_rows << ",\"nnz\":" << p.nnz << "}";
+  s << "{\"kind\":\"csr\",\"rows\":" << p.n_rows << ",\"nnz\":" << p.nnz << ",\"cols\":" << p.n_cols
+    << ",\"op\":" << static_cast<int>(p.op) << ",\"fuse_hist\":" << p.fuse_hist << ",\"bins\":" << p.n_bins
+    << ",\"shift\":" << p.hist_shift << ",\"fixed_class\":" << p.fixed_class
+    << ",\"class_limits\":[4,32,1024,16384],\"chunk\":" << kCsrChunk << "}";
   return s.str();
 }
 
+// ---------------------------------------------------------------- device code
+namespace {
+
+__device__ __forceinline__ int row_class(int64_t len, int fixed) {
+  if (fixed >= 0) return fixed;
+  if (len <= kCsrLimit0) return 0;
+  if (len <= kCsrLimit1) return 1;
+  if (len <= kCsrLimit2) return 2;
+  if (len <= kCsrLimit3) return 3;
+  return 4;
+}
+
+__device__ __forceinline__ int64_t n_chunks_of(int64_t len) { return len > 0 ? (len + kCsrChunk - 1) / kCsrChunk : 1; }
+
+__global__ void csr_zero_kernel(int64_t* counters, int n, long long* hist, int64_t n_bins) {
+  const int64_t i0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  if (i0 < n) counters[i0] = 0;
+  if (hist)
+    for (int64_t i = i0; i < n_bins; i += stride) hist[i] = 0;
+}
+
+// pass 1: rows per class and chunk slots of long rows (block-aggregated atomics)
+__global__ void csr_bin_count_kernel(const int64_t* __restrict__ off, int64_t n_rows, int fixed, int64_t* counters) {
+  __shared__ unsigned long long cnt[kCsrClasses + 1];
+  if (threadIdx.x <= kCsrClasses) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n_rows;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t len = off[i + 1] - off[i];
+    const int c = row_class(len, fixed);
+    atomicAdd(&cnt[c], 1ull);
+    if (c == 4) atomicAdd(&cnt[kCsrClasses], static_cast<unsigned long long>(n_chunks_of(len)));
+  }
+  __syncthreads();
+  if (threadIdx.x <= kCsrClasses && cnt[threadIdx.x])
+    atomicAdd(reinterpret_cast<unsigned long long*>(&counters[threadIdx.x]), cnt[threadIdx.x]);
+}
+
+// pass 2: scatter row ids into their class's range; reserve chunk slots of long rows
+__global__ void csr_bin_scatter_kernel(const int64_t* __restrict__ off, int64_t n_rows, int fixed, int64_t* counters,
+                                       int32_t* rows, int32_t* chunk_row, int32_t* chunk_idx, int32_t* chunk_base,
+                                       int32_t* chunk_cnt, int64_t max_chunks, int32_t* err) {
+  // class c occupies rows[start_c .. start_c + count_c); cursors live in counters[6 + c]
+  int64_t start[kCsrClasses];
+  int64_t acc = 0;
+#pragma unroll
+  for (int c = 0; c < kCsrClasses; ++c) {
+    start[c] = acc;
+    acc += counters[c];
+  }
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n_rows;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t len = off[i + 1] - off[i];
+    const int c = row_class(len, fixed);
+    const unsigned long long pos =
+        atomicAdd(reinterpret_cast<unsigned long long*>(&counters[6 + c]), 1ull);
+    rows[start[c] + static_cast<int64_t>(pos)] = static_cast<int32_t>(i);
+    if (c == 4) {
+      const int64_t nc = n_chunks_of(len);
+      const unsigned long long base =
+          atomicAdd(reinterpret_cast<unsigned long long*>(&counters[11]), static_cast<unsigned long long>(nc));
+      if (static_cast<int64_t>(base) + nc > max_chunks) {  // offsets disagree with the declared nnz
+        atomicExch(err, 2);
+        continue;
+      }
+      for (int64_t k = 0; k < nc; ++k) {
+        chunk_row[base + k] = static_cast<int32_t>(i);
+        chunk_idx[base + k] = static_cast<int32_t>(k);
+        chunk_base[base + k] = static_cast<int32_t>(base);
+        chunk_cnt[base + k] = static_cast<int32_t>(nc);
+      }
+    }
+  }
+}
+
+struct CsrArgs {
+  const int64_t* off;
+  const int32_t* col;
+  const float* val;
+  const float* x;
+  float* y;
+  long long* hist;      // fused histogram (global), or nullptr
+  int32_t* err;         // device error word: 2 = offsets or columns outside the declared sizes
+  int64_t nnz;
+  int64_t n_cols;
+  int shift;
+  int64_t n_bins;
+  int smem_bins;        // bins counted in shared memory (0: count straight into global memory)
+};
+
+__device__ __forceinline__ void hist_add(const CsrArgs& a, int* sh, int32_t c) {
+  const int64_t b = static_cast<int64_t>(c) >> a.shift;
+  if (b < a.n_bins) {
+    if (a.smem_bins) atomicAdd(&sh[b], 1);
+    else atomicAdd(reinterpret_cast<unsigned long long*>(&a.hist[b]), 1ull);
+  }
+}
+
+// fold entries s + t, s + t + L, ... < e into 4 accumulators (entry k goes to acc[(k / L) % 4])
+template <class Op, bool HIST>
+__device__ __forceinline__ void csr_fold(const CsrArgs& a, int* sh, int64_t s, int64_t e, int t, int L,
+                                         typename Op::Acc (&acc)[4]) {
+  if (s < 0 || e > a.nnz || s > e) {  // offsets outside [0, nnz]: flag, fold nothing
+    if (t == 0) atomicExch(a.err, 2);
+    return;
+  }
+  for (int64_t b = s + t; b < e; b += 4 * static_cast<int64_t>(L)) {
+    int32_t c[4];
+    float v[4];
+    bool ok[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t idx = b + static_cast<int64_t>(u) * L;
+      ok[u] = idx < e;
+      c[u] = ok[u] ? __ldcs(a.col + idx) : 0;
+      v[u] = ok[u] ? __ldcs(a.val + idx) : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (ok[u]) {
+        if (static_cast<uint32_t>(c[u]) < static_cast<uint64_t>(a.n_cols)) {
+          Op::add_prod(acc[u], v[u], __ldg(a.x + c[u]));
+          if constexpr (HIST) hist_add(a, sh, c[u]);
+        } else {
+          atomicExch(a.err, 2);
+        }
+      }
+    }
+  }
+}
+
+template <class Op>
+__device__ __forceinline__ typename Op::Acc fold4(const typename Op::Acc (&acc)[4]) {
+  return Op::combine(Op::combine(acc[0], acc[1]), Op::combine(acc[2], acc[3]));
+}
+
+template <class Op>
+__device__ __forceinline__ typename Op::Acc team_reduce(typename Op::Acc a, int width) {
+  for (int m = width >> 1; m >= 1; m >>= 1) a = Op::combine(a, Op::shfl_xor(a, m, width));
+  return a;
+}
+
+__device__ __forceinline__ void hist_init(int* sh, int bins) {
+  for (int i = threadIdx.x; i < bins; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+}
+
+__device__ __forceinline__ void hist_flush(const CsrArgs& a, int* sh) {
+  __syncthreads();
+  for (int i = threadIdx.x; i < a.smem_bins; i += blockDim.x)
+    if (sh[i]) atomicAdd(reinterpret_cast<unsigned long long*>(&a.hist[i]), static_cast<unsigned long long>(sh[i]));
+}
+
+// classes 0..2: a team of L lanes (1, 8 or 32) per row; persistent over the class list
+template <class Op, int L, bool HIST>
+__global__ void __launch_bounds__(256) csr_rows_kernel(CsrArgs a, const int32_t* __restrict__ rows, const int64_t* counters,
+                                                       int cls) {
+  extern __shared__ int sh_hist[];
+  if constexpr (HIST) {
+    if (a.smem_bins) hist_init(sh_hist, a.smem_bins);
+  }
+  int64_t start = 0;
+  for (int c = 0; c < cls; ++c) start += counters[c];
+  const int64_t count = counters[cls];
+  const int lane = threadIdx.x & 31;
+  const int lt = lane % L;
+  const int64_t team = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) / L;
+  const int64_t n_teams = static_cast<int64_t>(gridDim.x) * blockDim.x / L;
+  const int64_t warp_first_team = (blockIdx.x * static_cast<int64_t>(blockDim.x) + (threadIdx.x & ~31)) / L;
+  // every lane of a warp runs the same number of rounds (shuffles need the whole warp)
+  for (int64_t r0 = warp_first_team; r0 < count; r0 += n_teams) {
+    const int64_t k = r0 + (team - warp_first_team);
+    const bool valid = k < count;
+    typename Op::Acc acc[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] = Op::ident();
+    int32_t row = 0;
+    if (valid) {
+      row = rows[start + k];
+      csr_fold<Op, HIST>(a, sh_hist, a.off[row], a.off[row + 1], lt, L, acc);
+    }
+    typename Op::Acc r = fold4<Op>(acc);
+    if constexpr (L > 1) r = team_reduce<Op>(r, L);
+    if (valid && lt == 0) a.y[row] = Op::finish(r);
+  }
+  if constexpr (HIST) {
+    if (a.smem_bins) hist_flush(a, sh_hist);
+  }
+}
+
+// CTA-wide fold of one entry range; the result is valid in thread 0
+template <class Op, bool HIST>
+__device__ __forceinline__ typename Op::Acc cta_fold(const CsrArgs& a, int* sh, int64_t s, int64_t e,
+                                                     typename Op::Acc* wsh) {
+  typename Op::Acc acc[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) acc[u] = Op::ident();
+  csr_fold<Op, HIST>(a, sh, s, e, threadIdx.x, blockDim.x, acc);
+  typename Op::Acc r = team_reduce<Op>(fold4<Op>(acc), 32);
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0) wsh[warp] = r;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    r = wsh[0];
+    for (int w = 1; w < nw; ++w) r = Op::combine(r, wsh[w]);
+  }
+  __syncthreads();
+  return r;
+}
+
+// class 3: a CTA per row
+template <class Op, bool HIST>
+__global__ void __launch_bounds__(kCsrCtaThreads) csr_cta_kernel(CsrArgs a, const int32_t* __restrict__ rows,
+                                                                 const int64_t* counters) {
+  extern __shared__ int sh_hist[];
+  __shared__ typename Op::Acc wsh[kCsrCtaThreads / 32];
+  if constexpr (HIST) {
+    if (a.smem_bins) hist_init(sh_hist, a.smem_bins);
+  }
+  int64_t start = 0;
+  for (int c = 0; c < 3; ++c) start += counters[c];
+  const int64_t count = counters[3];
+  for (int64_t k = blockIdx.x; k < count; k += gridDim.x) {
+    const int32_t row = rows[start + k];
+    const typename Op::Acc r = cta_fold<Op, HIST>(a, sh_hist, a.off[row], a.off[row + 1], wsh);
+    if (threadIdx.x == 0) a.y[row] = Op::finish(r);
+  }
+  if constexpr (HIST) {
+    if (a.smem_bins) hist_flush(a, sh_hist);
+  }
+}
+
+// class 4: a CTA per chunk of a long row; the last chunk to finish folds the row
+template <class Op, bool HIST>
+__global__ void __launch_bounds__(kCsrCtaThreads) csr_split_kernel(CsrArgs a, const int64_t* counters,
+                                                                   const int32_t* __restrict__ chunk_row,
+                                                                   const int32_t* __restrict__ chunk_idx,
+                                                                   const int32_t* __restrict__ chunk_base,
+                                                                   const int32_t* __restrict__ chunk_cnt,
+                                                                   int32_t* tickets, typename Op::Acc* part,
+                                                                   int64_t max_chunks) {
+  extern __shared__ int sh_hist[];
+  __shared__ typename Op::Acc wsh[kCsrCtaThreads / 32];
+  __shared__ int last;
+  if constexpr (HIST) {
+    if (a.smem_bins) hist_init(sh_hist, a.smem_bins);
+  }
+  const int64_t n_slots = counters[11] < max_chunks ? counters[11] : max_chunks;
+  for (int64_t k = blockIdx.x; k < n_slots; k += gridDim.x) {
+    const int32_t row = chunk_row[k];
+    const int64_t c = chunk_idx[k];
+    const int64_t s = a.off[row] + c * kCsrChunk;
+    const int64_t e0 = a.off[row + 1];
+    const int64_t e = (s + kCsrChunk < e0) ? s + kCsrChunk : e0;
+    const typename Op::Acc r = cta_fold<Op, HIST>(a, sh_hist, s, e, wsh);
+    if (threadIdx.x == 0) {
+      part[k] = r;
+      __threadfence();   // publish the partial before taking a ticket
+      const int base = chunk_base[k], n = chunk_cnt[k];
+      last = (atomicAdd(&tickets[base], 1) == n - 1) ? 1 : 0;
+      if (last) {
+        __threadfence();  // every other chunk's partial is visible
+        if constexpr (sizeof(typename Op::Acc) == 8 && Op::kFp) {
+          double sum = 0.0;
+          for (int q = 0; q < n; ++q) {
+            const volatile float* pv = reinterpret_cast<const volatile float*>(part) + 2 * (base + q);
+            sum += static_cast<double>(pv[0]);
+            sum += static_cast<double>(pv[1]);
+          }
+          a.y[row] = static_cast<float>(sum);
+        } else {
+          typename Op::Acc v = *reinterpret_cast<volatile typename Op::Acc*>(part + base);
+          for (int q = 1; q < n; ++q) v = Op::combine(v, *reinterpret_cast<volatile typename Op::Acc*>(part + base + q));
+          a.y[row] = Op::finish(v);
+        }
+        tickets[base] = 0;  // ready for the next run
+      }
+    }
+    __syncthreads();
+  }
+  if constexpr (HIST) {
+    if (a.smem_bins) hist_flush(a, sh_hist);
+  }
+}
+
+// standalone count histogram over all entries
+__global__ void __launch_bounds__(256) csr_hist_kernel(const int32_t* __restrict__ col, int64_t nnz, int shift,
+                                                       int64_t n_bins, int smem_bins, long long* hist) {
+  extern __shared__ int sh_hist[];
+  if (smem_bins) hist_init(sh_hist, smem_bins);
+  CsrArgs a{};
+  a.hist = hist;
+  a.shift = shift;
+  a.n_cols = 0;
+  a.n_bins = n_bins;
+  a.smem_bins = smem_bins;
+  const int64_t n4 = nnz / 4;
+  const int4* col4 = reinterpret_cast<const int4*>(col);
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n4;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int4 c = __ldcs(col4 + i);
+    hist_add(a, sh_hist, c.x);
+    hist_add(a, sh_hist, c.y);
+    hist_add(a, sh_hist, c.z);
+    hist_add(a, sh_hist, c.w);
+  }
+  for (int64_t i = n4 * 4 + blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < nnz;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    hist_add(a, sh_hist, __ldcs(col + i));
+  if (smem_bins) hist_flush(a, sh_hist);
+}
+
+inline hp_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(HP_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <class K>
+hp_status set_smem(K kernel, size_t dyn) {
+  if (dyn == 0) return HP_OK;
+  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
+  return e == cudaSuccess ? HP_OK : cuda_fail(e, "CSR kernel shared memory");
+}
+
+template <class Op, bool HIST>
+hp_status launch_classes(hp_nest* n, const CsrArgs& a, cudaStream_t st) {
+  CsrState& cs = *n->cs;
+  const size_t dyn = HIST ? static_cast<size_t>(a.smem_bins) * sizeof(int) : 0;
+  hp_status s;
+  if ((s = set_smem(csr_rows_kernel<Op, 1, HIST>, dyn)) != HP_OK) return s;
+  if ((s = set_smem(csr_rows_kernel<Op, 8, HIST>, dyn)) != HP_OK) return s;
+  if ((s = set_smem(csr_rows_kernel<Op, 32, HIST>, dyn)) != HP_OK) return s;
+  if ((s = set_smem(csr_cta_kernel<Op, HIST>, dyn)) != HP_OK) return s;
+  if ((s = set_smem(csr_split_kernel<Op, HIST>, dyn)) != HP_OK) return s;
+  const int fixed = n->csr.fixed_class;
+  if (fixed < 0 || fixed == 0) csr_rows_kernel<Op, 1, HIST><<<cs.grid_rows, 256, dyn, st>>>(a, cs.rows, cs.counters, 0);
+  if (fixed < 0 || fixed == 1) csr_rows_kernel<Op, 8, HIST><<<cs.grid_rows, 256, dyn, st>>>(a, cs.rows, cs.counters, 1);
+  if (fixed < 0 || fixed == 2) csr_rows_kernel<Op, 32, HIST><<<cs.grid_rows, 256, dyn, st>>>(a, cs.rows, cs.counters, 2);
+  if (fixed < 0 || fixed == 3) csr_cta_kernel<Op, HIST><<<cs.grid_cta, kCsrCtaThreads, dyn, st>>>(a, cs.rows, cs.counters);
+  if (fixed < 0 || fixed == 4)
+    csr_split_kernel<Op, HIST><<<cs.grid_cta, kCsrCtaThreads, dyn, st>>>(
+        a, cs.counters, cs.chunk_row, cs.chunk_idx, cs.chunk_base, cs.chunk_cnt, cs.tickets,
+        static_cast<typename Op::Acc*>(cs.part), cs.max_chunks);
+  const cudaError_t e = cudaPeekAtLastError();
+  return e == cudaSuccess ? HP_OK : cuda_fail(e, "CSR class kernel launch");
+}
+
+template <class Op>
+hp_status launch_op(hp_nest* n, const CsrArgs& a, cudaStream_t st) {
+  return a.hist ? launch_classes<Op, true>(n, a, st) : launch_classes<Op, false>(n, a, st);
+}
+
+int smem_bins_for(int64_t n_bins) { return n_bins <= kCsrHistSmemMax ? static_cast<int>(n_bins) : 0; }
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
 hp_status csr_prepare(hp_nest* n) {
-  (void)n;
+  const CsrPlan& p = n->csr;
+  CsrState* cs = new (std::nothrow) CsrState();
+  if (!cs) return fail(HP_ENOMEM, "host allocation failed");
+  n->cs = cs;
+  cudaError_t e;
+  e = cudaMalloc(&cs->counters, 16 * sizeof(int64_t));
+  if (e != cudaSuccess) return fail(HP_ENOMEM, "cudaMalloc (CSR counters)");
+  if (p.op == HP_RED_HIST_COUNT) return HP_OK;
+  const int64_t rows = std::max<int64_t>(p.n_rows, 1);
+  // long rows have > kCsrChunk entries, so chunk slots <= 2 * nnz / kCsrChunk + 1
+  cs->max_chunks = 2 * (p.nnz / kCsrChunk) + 2;
+  if (p.fixed_class == 4) cs->max_chunks = p.nnz / kCsrChunk + p.n_rows + 2;
+  e = cudaMalloc(&cs->rows, rows * sizeof(int32_t));
+  if (e != cudaSuccess) return fail(HP_ENOMEM, "cudaMalloc (CSR row lists)");
+  const size_t mc = static_cast<size_t>(cs->max_chunks);
+  if (cudaMalloc(&cs->chunk_row, mc * sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc(&cs->chunk_idx, mc * sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc(&cs->chunk_base, mc * sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc(&cs->chunk_cnt, mc * sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc(&cs->tickets, mc * sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc(&cs->part, mc * sizeof(f2)) != cudaSuccess)
+    return fail(HP_ENOMEM, "cudaMalloc (CSR chunk tables)");
+  // every slot starts as a valid (row 0, chunk 0) entry, so a slot the binning
+  // could not fill (offsets beyond the declared nnz, flagged) reads in bounds
+  for (int32_t* t : {cs->tickets, cs->chunk_row, cs->chunk_idx, cs->chunk_base, cs->chunk_cnt}) {
+    e = cudaMemset(t, 0, mc * sizeof(int32_t));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemset (chunk tables)");
+  }
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, csr_rows_kernel<OpF32Comp, 32, true>, 256,
+                                                smem_bins_for(p.n_bins) * sizeof(int));
+  cs->grid_rows = std::max(1, per_sm) * n->sms;
+  per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, csr_split_kernel<OpF32Comp, true>, kCsrCtaThreads,
+                                                smem_bins_for(p.n_bins) * sizeof(int));
+  cs->grid_cta = std::max(1, per_sm) * n->sms;
   return HP_OK;
 }
 
 hp_status run_csr(hp_nest* n, const void* const* in_dev, void* out_dev, cudaStream_t st) {
-  (void)n;
-  (void)in_dev;
-  (void)out_dev;
-  (void)st;
-  return fail(HP_EUNSUPPORTED, "CSR execution is not built yet");
+  const CsrPlan& p = n->csr;
+  CsrState& cs = *n->cs;
+  if (!in_dev) return fail(HP_EINVAL, "in_dev is NULL");
+  if (!out_dev) return fail(HP_EINVAL, "out_dev is NULL");
+  if (p.op == HP_RED_HIST_COUNT) {
+    const int32_t* col = static_cast<const int32_t*>(in_dev[1]);
+    if (!col && p.nnz > 0) return fail(HP_EINVAL, "missing col");
+    if (reinterpret_cast<uintptr_t>(col) & 15u) return fail(HP_EINVAL, "col must be 16-byte aligned");
+    long long* hist = static_cast<long long*>(out_dev);
+    csr_zero_kernel<<<std::max<int64_t>(1, std::min<int64_t>((p.n_bins + 255) / 256, 4 * n->sms)), 256, 0, st>>>(
+        cs.counters, 0, hist, p.n_bins);
+    const int sb = smem_bins_for(p.n_bins);
+    const size_t dyn = static_cast<size_t>(sb) * sizeof(int);
+    hp_status s = set_smem(csr_hist_kernel, dyn);
+    if (s != HP_OK) return s;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, csr_hist_kernel, 256, dyn);
+    const int64_t want = (p.nnz / 4 + 255) / 256;
+    const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(want, std::max(1, per_sm) * n->sms)));
+    csr_hist_kernel<<<grid, 256, dyn, st>>>(col, p.nnz, p.hist_shift, p.n_bins, sb, hist);
+    const cudaError_t e = cudaPeekAtLastError();
+    return e == cudaSuccess ? HP_OK : cuda_fail(e, "CSR histogram launch");
+  }
+  for (int i = 0; i < 4; ++i)
+    if (!in_dev[i]) return fail(HP_EINVAL, "missing CSR input " + std::to_string(i));
+  CsrArgs a{};
+  a.off = static_cast<const int64_t*>(in_dev[0]);
+  a.col = static_cast<const int32_t*>(in_dev[1]);
+  a.val = static_cast<const float*>(in_dev[2]);
+  a.x = static_cast<const float*>(in_dev[3]);
+  a.y = static_cast<float*>(out_dev);
+  a.hist = nullptr;
+  a.err = n->err;
+  a.nnz = p.nnz;
+  a.n_cols = p.n_cols;
+  if (p.fuse_hist) {
+    a.hist = static_cast<long long*>(const_cast<void*>(in_dev[4]));
+    if (!a.hist) return fail(HP_EINVAL, "fuse_hist needs the histogram output in in_dev[4]");
+    a.shift = p.hist_shift;
+    a.n_bins = p.n_bins;
+    a.smem_bins = smem_bins_for(p.n_bins);
+  }
+  if (p.n_rows == 0) return HP_OK;
+  const int zgrid = static_cast<int>(
+      std::max<int64_t>(1, std::min<int64_t>((std::max<int64_t>(p.fuse_hist ? p.n_bins : 0, 16) + 255) / 256, 4 * n->sms)));
+  csr_zero_kernel<<<zgrid, 256, 0, st>>>(cs.counters, 16, a.hist, p.fuse_hist ? p.n_bins : 0);
+  const int bgrid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((p.n_rows + kCsrBinThreads - 1) / kCsrBinThreads,
+                                                                           8 * n->sms)));
+  csr_bin_count_kernel<<<bgrid, kCsrBinThreads, 0, st>>>(a.off, p.n_rows, p.fixed_class, cs.counters);
+  csr_bin_scatter_kernel<<<bgrid, kCsrBinThreads, 0, st>>>(a.off, p.n_rows, p.fixed_class, cs.counters, cs.rows,
+                                                          cs.chunk_row, cs.chunk_idx, cs.chunk_base, cs.chunk_cnt,
+                                                          cs.max_chunks, n->err);
+  cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "CSR binning launch");
+  switch (p.op) {
+    case HP_RED_SUM:
+      return p.prec == HP_F32_COMP ? launch_op<OpF32Comp>(n, a, st) : launch_op<OpF32Sum>(n, a, st);
+    case HP_RED_MAX:
+      return launch_op<OpF32Max>(n, a, st);
+    case HP_RED_MIN:
+      return launch_op<OpF32Min>(n, a, st);
+    default:
+      return fail(HP_EINVAL, "bad CSR op");
+  }
 }
 
-size_t csr_out_bytes(const hp_nest* n) { return static_cast<size_t>(n->csr.n_rows) * 4; }
+size_t csr_out_bytes(const hp_nest* n) {
+  return n->csr.op == HP_RED_HIST_COUNT ? static_cast<size_t>(n->csr.n_bins) * 8
+                                        : static_cast<size_t>(n->csr.n_rows) * 4;
+}
 
 void csr_release(hp_nest* n) {
-  delete n->cs;
+  CsrState* cs = n->cs;
+  if (!cs) return;
+  cudaFree(cs->counters);
+  cudaFree(cs->rows);
+  cudaFree(cs->chunk_row);
+  cudaFree(cs->chunk_idx);
+  cudaFree(cs->chunk_base);
+  cudaFree(cs->chunk_cnt);
+  cudaFree(cs->tickets);
+  cudaFree(cs->part);
+  delete cs;
   n->cs = nullptr;
 }
 

@@ -81,6 +81,7 @@ struct CsrPlan {
   int64_t n_rows = 0, nnz = 0, n_cols = 0, n_bins = 0;
   int32_t hist_shift = 0;
   int32_t fuse_hist = 0;
+  int32_t fixed_class = -1;   // -1: rows binned by length; else every row in this class
   hp_red_op op = HP_RED_SUM;
   hp_prec prec = HP_F32;
 };
