@@ -365,6 +365,91 @@ def run_profile_case(args):
     n.close()
 
 
+def _event_time(fn, steps, warmup, stream, flush=None):
+    """Mean ms per call of fn() on `stream`, CUDA events; optional L2 flush between calls."""
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        per = []
+        for _ in range(steps):
+            if flush is not None:
+                flush()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            per.append((e0, e1))
+        torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in per]))
+
+
+def run_csr_workload(args):
+    """Ragged CSR nest: 2^22 rows (or --csr-rows), Zipf(1.5) lengths clipped to
+    [1, 65536], col uniform in [0, 2^22), FP32 normal val / x, compensated SpMV
+    with the int64 histogram of col >> 10 fused into the same sweep."""
+    import torch
+
+    from paper_2309_01906_gb300 import binding as hb
+    from paper_2309_01906_gb300 import synth
+    n_rows = args.csr_rows
+    n_cols = 1 << 22
+    csr = synth.csr_zipf(n_rows=n_rows, n_cols=n_cols)
+    n_bins = n_cols >> 10
+    d = [torch.from_numpy(a).cuda() for a in (csr.offsets, csr.col, csr.val, csr.x)]
+    y = torch.empty(n_rows, dtype=torch.float32, device="cuda")
+    h = torch.empty(n_bins, dtype=torch.int64, device="cuda")
+    p = hb.hp_csr_params(csr.nnz, n_cols, 10, 0 if args.no_hist else 1, n_bins)
+    n = hb.Nest(csr_rows=n_rows, red_level=1, op="sum", prec=args.prec, body="csr_gather", params=p)
+    stream = torch.cuda.Stream()
+    ins = [t.data_ptr() for t in d] + [h.data_ptr()]
+    ms = _event_time(lambda: n.run(ins, y.data_ptr(), stream.cuda_stream), args.steps, args.warmup, stream)
+    assert n.check(stream.cuda_stream) == 0
+    alg = 8 * csr.nnz + 8 * (n_rows + 1) + 4 * n_cols + 4 * n_rows + 8 * n_bins
+    peak, kind = measured_peaks()
+    lens = np.diff(csr.offsets)
+    print(json.dumps({
+        "workload": f"CSR {n_rows} rows, Zipf(1.5) clipped [1,65536], nnz {csr.nnz}, SpMV"
+                    + ("" if args.no_hist else " + fused int64 histogram"),
+        "metric": "nest iterations/s", "value": csr.nnz / (ms * 1e-3), "unit": "iterations/s",
+        "ms_per_step": ms, "prec": args.prec, "steps": args.steps, "warmup": args.warmup,
+        "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": alg / (ms * 1e-3) / 1e9 / peak, "peak_kind": kind, "algorithmic_bytes": alg},
+        "x_gather_sector_bytes": 32 * csr.nnz,
+        "rows_by_class": [int(np.sum(lens <= 4)), int(np.sum((lens > 4) & (lens <= 32))),
+                          int(np.sum((lens > 32) & (lens <= 1024))), int(np.sum((lens > 1024) & (lens <= 16384))),
+                          int(np.sum(lens > 16384))],
+        "l2": "inputs larger than L2; no flush"}))
+    n.close()
+
+
+def run_gemv_workload(args):
+    """2-level nest 1024 x 1024 (GEMV-shaped), FP32 and int32, one launch; L2 flushed
+    between timed launches (a 256 MiB write) and also timed warm."""
+    import torch
+
+    from paper_2309_01906_gb300 import binding as hb
+    from paper_2309_01906_gb300 import synth
+    stream = torch.cuda.Stream()
+    scrub = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+    res = {}
+    for prec, (A, x) in (("f32_comp", synth.gemv_f32()), ("f32", synth.gemv_f32()), ("i32", synth.gemv_i32())):
+        dA = torch.from_numpy(A.reshape(-1)).cuda()
+        dx = torch.from_numpy(x).cuda()
+        out = torch.empty(1024, dtype=torch.int32 if prec == "i32" else torch.float32, device="cuda")
+        n = hb.Nest([1024, 1024], 1, "sum", prec, "dot_bcast", level_map=["grid", "warp"])
+        run = lambda: n.run([dA.data_ptr(), dx.data_ptr()], out.data_ptr(), stream.cuda_stream)  # noqa: E731
+        cold = _event_time(run, args.steps, args.warmup, stream, flush=lambda: scrub.fill_(1.0))
+        warm = _event_time(run, args.steps, args.warmup, stream)
+        res[prec] = {"cold_us": cold * 1e3, "warm_us": warm * 1e3,
+                     "iterations_per_s_cold": (1 << 20) / (cold * 1e-3)}
+        n.close()
+    print(json.dumps({"workload": "2-level nest 1024 x 1024, out[i] = sum_j A[i][j] * x[j], one launch",
+                      "map": "i -> grid, j -> warp (lanes x 4 vector slots)", "results": res,
+                      "algorithmic_bytes": 4 * (1 << 20) + 2 * 4096}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -377,6 +462,10 @@ def main():
     ap.add_argument("--profile-b", type=int, default=0,
                     help="profiler case: run only the headline nest with this outer extent b")
     ap.add_argument("--prec", default="f32_comp", choices=["f32_comp", "f32"])
+    ap.add_argument("--workload", default="nest4", choices=["nest4", "csr", "gemv"],
+                    help="nest4: the headline line; csr / gemv: measurement of the other workloads")
+    ap.add_argument("--csr-rows", type=int, default=1 << 22)
+    ap.add_argument("--no-hist", action="store_true", help="csr: SpMV without the fused histogram")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -384,6 +473,10 @@ def main():
         run_reference(args)
     elif args.profile_b:
         run_profile_case(args)
+    elif args.workload == "csr":
+        run_csr_workload(args)
+    elif args.workload == "gemv":
+        run_gemv_workload(args)
     else:
         run_hp(args)
 

@@ -140,16 +140,27 @@ __global__ void csr_zero_kernel(int64_t* counters, int n, long long* hist, int64
     for (int64_t i = i0; i < n_bins; i += stride) hist[i] = 0;
 }
 
-// pass 1: rows per class and chunk slots of long rows (block-aggregated atomics)
+// pass 1: rows per class and chunk slots of long rows (warp ballots, one
+// shared-memory add per warp and class, one global add per block and class)
 __global__ void csr_bin_count_kernel(const int64_t* __restrict__ off, int64_t n_rows, int fixed, int64_t* counters) {
   __shared__ unsigned long long cnt[kCsrClasses + 1];
   if (threadIdx.x <= kCsrClasses) cnt[threadIdx.x] = 0;
   __syncthreads();
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n_rows;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t len = off[i + 1] - off[i];
-    const int c = row_class(len, fixed);
-    atomicAdd(&cnt[c], 1ull);
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t tile = blockIdx.x * static_cast<int64_t>(blockDim.x); tile < n_rows; tile += stride) {
+    const int64_t i = tile + threadIdx.x;
+    int c = -1;
+    int64_t len = 0;
+    if (i < n_rows) {
+      len = off[i + 1] - off[i];
+      c = row_class(len, fixed);
+    }
+#pragma unroll
+    for (int k = 0; k < kCsrClasses; ++k) {
+      const unsigned m = __ballot_sync(0xffffffffu, c == k);
+      if (lane == 0 && m) atomicAdd(&cnt[k], static_cast<unsigned long long>(__popc(m)));
+    }
     if (c == 4) atomicAdd(&cnt[kCsrClasses], static_cast<unsigned long long>(n_chunks_of(len)));
   }
   __syncthreads();
@@ -157,10 +168,15 @@ __global__ void csr_bin_count_kernel(const int64_t* __restrict__ off, int64_t n_
     atomicAdd(reinterpret_cast<unsigned long long*>(&counters[threadIdx.x]), cnt[threadIdx.x]);
 }
 
-// pass 2: scatter row ids into their class's range; reserve chunk slots of long rows
-__global__ void csr_bin_scatter_kernel(const int64_t* __restrict__ off, int64_t n_rows, int fixed, int64_t* counters,
-                                       int32_t* rows, int32_t* chunk_row, int32_t* chunk_idx, int32_t* chunk_base,
-                                       int32_t* chunk_cnt, int64_t max_chunks, int32_t* err) {
+// pass 2: scatter row ids into their class's range (tile by tile: warp ballots
+// give each row its rank, one global add per block and class reserves the
+// tile's range); reserve chunk slots of long rows
+__global__ void __launch_bounds__(kCsrBinThreads) csr_bin_scatter_kernel(
+    const int64_t* __restrict__ off, int64_t n_rows, int fixed, int64_t* counters, int32_t* rows, int32_t* chunk_row,
+    int32_t* chunk_idx, int32_t* chunk_base, int32_t* chunk_cnt, int64_t max_chunks, int32_t* err) {
+  constexpr int kWarps = kCsrBinThreads / 32;
+  __shared__ int wpos[kWarps][kCsrClasses];
+  __shared__ long long bbase[kCsrClasses];
   // class c occupies rows[start_c .. start_c + count_c); cursors live in counters[6 + c]
   int64_t start[kCsrClasses];
   int64_t acc = 0;
@@ -169,28 +185,55 @@ __global__ void csr_bin_scatter_kernel(const int64_t* __restrict__ off, int64_t 
     start[c] = acc;
     acc += counters[c];
   }
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n_rows;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t len = off[i + 1] - off[i];
-    const int c = row_class(len, fixed);
-    const unsigned long long pos =
-        atomicAdd(reinterpret_cast<unsigned long long*>(&counters[6 + c]), 1ull);
-    rows[start[c] + static_cast<int64_t>(pos)] = static_cast<int32_t>(i);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t tile = blockIdx.x * static_cast<int64_t>(blockDim.x); tile < n_rows; tile += stride) {
+    const int64_t i = tile + threadIdx.x;
+    int c = -1;
+    int64_t len = 0;
+    if (i < n_rows) {
+      len = off[i + 1] - off[i];
+      c = row_class(len, fixed);
+    }
+    int rank = 0;
+#pragma unroll
+    for (int k = 0; k < kCsrClasses; ++k) {
+      const unsigned m = __ballot_sync(0xffffffffu, c == k);
+      if (lane == 0) wpos[warp][k] = __popc(m);
+      if (c == k) rank = __popc(m & lt_mask);
+    }
+    __syncthreads();
+    if (threadIdx.x < kCsrClasses) {
+      int tot = 0;
+      for (int w = 0; w < kWarps; ++w) {
+        const int v = wpos[w][threadIdx.x];
+        wpos[w][threadIdx.x] = tot;
+        tot += v;
+      }
+      bbase[threadIdx.x] =
+          tot ? static_cast<long long>(atomicAdd(reinterpret_cast<unsigned long long*>(&counters[6 + threadIdx.x]),
+                                                 static_cast<unsigned long long>(tot)))
+              : 0;
+    }
+    __syncthreads();
+    if (c >= 0) rows[start[c] + bbase[c] + wpos[warp][c] + rank] = static_cast<int32_t>(i);
     if (c == 4) {
       const int64_t nc = n_chunks_of(len);
       const unsigned long long base =
           atomicAdd(reinterpret_cast<unsigned long long*>(&counters[11]), static_cast<unsigned long long>(nc));
       if (static_cast<int64_t>(base) + nc > max_chunks) {  // offsets disagree with the declared nnz
         atomicExch(err, 2);
-        continue;
-      }
-      for (int64_t k = 0; k < nc; ++k) {
-        chunk_row[base + k] = static_cast<int32_t>(i);
-        chunk_idx[base + k] = static_cast<int32_t>(k);
-        chunk_base[base + k] = static_cast<int32_t>(base);
-        chunk_cnt[base + k] = static_cast<int32_t>(nc);
+      } else {
+        for (int64_t k = 0; k < nc; ++k) {
+          chunk_row[base + k] = static_cast<int32_t>(i);
+          chunk_idx[base + k] = static_cast<int32_t>(k);
+          chunk_base[base + k] = static_cast<int32_t>(base);
+          chunk_cnt[base + k] = static_cast<int32_t>(nc);
+        }
       }
     }
+    __syncthreads();  // wpos / bbase are reused by the next tile
   }
 }
 
@@ -250,6 +293,74 @@ __device__ __forceinline__ void csr_fold(const CsrArgs& a, int* sh, int64_t s, i
   }
 }
 
+template <class Op, bool HIST>
+__device__ __forceinline__ void csr_fold_one(const CsrArgs& a, int* sh, int64_t idx, typename Op::Acc& acc) {
+  const int32_t c = __ldcs(a.col + idx);
+  const float v = __ldcs(a.val + idx);
+  if (static_cast<uint32_t>(c) < static_cast<uint64_t>(a.n_cols)) {
+    Op::add_prod(acc, v, __ldg(a.x + c));
+    if constexpr (HIST) hist_add(a, sh, c);
+  } else {
+    atomicExch(a.err, 2);
+  }
+}
+
+template <class Op, bool HIST>
+__device__ __forceinline__ void csr_fold_group(const CsrArgs& a, int* sh, const int4& c, const float4& v,
+                                               typename Op::Acc (&acc)[4]) {
+  const int32_t cc[4] = {c.x, c.y, c.z, c.w};
+  const float vv[4] = {v.x, v.y, v.z, v.w};
+  float xv[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    xv[u] = (static_cast<uint32_t>(cc[u]) < static_cast<uint64_t>(a.n_cols)) ? __ldg(a.x + cc[u]) : 0.0f;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    if (static_cast<uint32_t>(cc[u]) < static_cast<uint64_t>(a.n_cols)) {
+      Op::add_prod(acc[u], vv[u], xv[u]);
+      if constexpr (HIST) hist_add(a, sh, cc[u]);
+    } else {
+      atomicExch(a.err, 2);
+    }
+  }
+}
+
+// Entries [s, e) for wide teams: the 16-byte-aligned middle is read as 128-bit
+// groups of col and val (lane t takes groups g0 + t, g0 + t + L, ..., two at a
+// time so that 8 gathers of x are in flight), the unaligned head and tail
+// (< 4 entries each) by lanes 0..3 into their first and second accumulators.
+// The tree depends only on (s, e), so a row's result is reproducible.
+template <class Op, bool HIST>
+__device__ __forceinline__ void csr_fold_vec(const CsrArgs& a, int* sh, int64_t s, int64_t e, int t, int L,
+                                             typename Op::Acc (&acc)[4]) {
+  if (s < 0 || e > a.nnz || s > e) {
+    if (t == 0) atomicExch(a.err, 2);
+    return;
+  }
+  const int64_t g0 = (s + 3) >> 2, g1 = e >> 2;
+  if (g0 >= g1) {
+    csr_fold<Op, HIST>(a, sh, s, e, t, L, acc);
+    return;
+  }
+  if (t < 4 * g0 - s) csr_fold_one<Op, HIST>(a, sh, s + t, acc[0]);
+  if (t < e - 4 * g1) csr_fold_one<Op, HIST>(a, sh, 4 * g1 + t, acc[1]);
+  const int4* col4 = reinterpret_cast<const int4*>(a.col);
+  const float4* val4 = reinterpret_cast<const float4*>(a.val);
+  for (int64_t g = g0 + t; g < g1; g += 2 * static_cast<int64_t>(L)) {
+    const bool two = g + L < g1;
+    const int4 c0 = __ldcs(col4 + g);
+    const float4 v0 = __ldcs(val4 + g);
+    int4 c1 = make_int4(0, 0, 0, 0);
+    float4 v1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (two) {
+      c1 = __ldcs(col4 + g + L);
+      v1 = __ldcs(val4 + g + L);
+    }
+    csr_fold_group<Op, HIST>(a, sh, c0, v0, acc);
+    if (two) csr_fold_group<Op, HIST>(a, sh, c1, v1, acc);
+  }
+}
+
 template <class Op>
 __device__ __forceinline__ typename Op::Acc fold4(const typename Op::Acc (&acc)[4]) {
   return Op::combine(Op::combine(acc[0], acc[1]), Op::combine(acc[2], acc[3]));
@@ -298,7 +409,8 @@ __global__ void __launch_bounds__(256) csr_rows_kernel(CsrArgs a, const int32_t*
     int32_t row = 0;
     if (valid) {
       row = rows[start + k];
-      csr_fold<Op, HIST>(a, sh_hist, a.off[row], a.off[row + 1], lt, L, acc);
+      if constexpr (L == 32) csr_fold_vec<Op, HIST>(a, sh_hist, a.off[row], a.off[row + 1], lt, L, acc);
+      else csr_fold<Op, HIST>(a, sh_hist, a.off[row], a.off[row + 1], lt, L, acc);
     }
     typename Op::Acc r = fold4<Op>(acc);
     if constexpr (L > 1) r = team_reduce<Op>(r, L);
@@ -316,7 +428,7 @@ __device__ __forceinline__ typename Op::Acc cta_fold(const CsrArgs& a, int* sh, 
   typename Op::Acc acc[4];
 #pragma unroll
   for (int u = 0; u < 4; ++u) acc[u] = Op::ident();
-  csr_fold<Op, HIST>(a, sh, s, e, threadIdx.x, blockDim.x, acc);
+  csr_fold_vec<Op, HIST>(a, sh, s, e, threadIdx.x, blockDim.x, acc);
   typename Op::Acc r = team_reduce<Op>(fold4<Op>(acc), 32);
   const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if ((threadIdx.x & 31) == 0) wsh[warp] = r;
@@ -541,6 +653,8 @@ hp_status run_csr(hp_nest* n, const void* const* in_dev, void* out_dev, cudaStre
   }
   for (int i = 0; i < 4; ++i)
     if (!in_dev[i]) return fail(HP_EINVAL, "missing CSR input " + std::to_string(i));
+  if ((reinterpret_cast<uintptr_t>(in_dev[1]) | reinterpret_cast<uintptr_t>(in_dev[2])) & 15u)
+    return fail(HP_EINVAL, "CSR col and val must be 16-byte aligned (128-bit loads)");
   CsrArgs a{};
   a.off = static_cast<const int64_t*>(in_dev[0]);
   a.col = static_cast<const int32_t*>(in_dev[1]);

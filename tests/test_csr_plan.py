@@ -66,3 +66,34 @@ def model_row_cover(length, lanes, chunk=16384, split=False):
 def test_row_cover_once(length, lanes, split):
     seen = model_row_cover(length, lanes, split=split)
     assert np.all(seen == 1)
+
+
+def model_vec_cover(s, e, lanes):
+    """Entries lanes fold in the 128-bit path (aligned middle, scalar head / tail)."""
+    seen = {}
+    g0, g1 = (s + 3) >> 2, e >> 2
+    if g0 >= g1:
+        return None
+    for t in range(lanes):
+        if t < 4 * g0 - s:
+            seen[s + t] = seen.get(s + t, 0) + 1
+        if t < e - 4 * g1:
+            seen[4 * g1 + t] = seen.get(4 * g1 + t, 0) + 1
+        g = g0 + t
+        while g < g1:
+            for gg in (g, g + lanes):
+                if gg < g1 and (gg == g or True):
+                    for k in range(4):
+                        seen[4 * gg + k] = seen.get(4 * gg + k, 0) + 1
+            g += 2 * lanes
+    return seen
+
+
+@pytest.mark.parametrize("s", [0, 1, 2, 3, 5, 1000, 1001])
+@pytest.mark.parametrize("length,lanes", [(8, 32), (33, 32), (1024, 32), (1025, 256), (16385, 256), (7, 32)])
+def test_vector_fold_covers_once(s, length, lanes):
+    e = s + length
+    seen = model_vec_cover(s, e, lanes)
+    if seen is None:
+        return   # short range: the scalar path (covered above)
+    assert sorted(seen) == list(range(s, e)) and set(seen.values()) == {1}
