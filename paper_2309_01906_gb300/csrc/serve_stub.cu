@@ -4,11 +4,6 @@
 using namespace hp;
 
 extern "C" {
-hp_status hp_nest_run_batch(hp_nest* const* nests, const void* const* const* in_dev, void* const* out_dev, int count,
-                            void* stream) {
-  (void)nests; (void)in_dev; (void)out_dev; (void)count; (void)stream;
-  return fail(HP_EUNSUPPORTED, "batched execution is not built yet");
-}
 hp_status hp_serve_create(size_t mem_budget_bytes, int max_slots, int n_streams, hp_server** out) {
   (void)mem_budget_bytes; (void)max_slots; (void)n_streams; (void)out;
   return fail(HP_EUNSUPPORTED, "serving is not built yet");
