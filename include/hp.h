@@ -226,6 +226,25 @@ hp_status hp_nest_run_static(hp_nest *n, const void *const *in_dev, void *out_de
 hp_status hp_nest_run_batch(hp_nest *const *nests, const void *const *const *in_dev, void *const *out_dev,
                             int count, void *stream);
 
+/*
+ * Autotune the level -> hardware binding of a rectangular nest (Sec. 3.2
+ * selects levels by property, Sec. 3.3 compiles a region for several
+ * candidate levels and picks one at run time; here the pick is timed).
+ * Candidates keep the output levels on the grid and bind every reduced level
+ * to one hardware level (CTA of 4 or 8 warps, warp, sub-warp group of 2..16
+ * lanes, the vector slots of a thread, a thread, or a split over grid parts);
+ * each is run on in_dev / out_dev on `stream` and timed with CUDA events.
+ * The fastest is installed in n and stored for the nest's shape class (log2
+ * of the output count and of the reduced size, 128-bit divisibility, body,
+ * precision, operator); nests created later with map == NULL take it.
+ * flags bit 0: re-time even if the class is already tuned.
+ * Synchronous (waits for the stream).  On return out_dev holds the installed
+ * plan's result.  The GEOMETRIC body is not tuned.  Tune a nest before
+ * passing it to hp_nest_run_batch or a server; batches built earlier with it
+ * are rebuilt on their next call.
+ */
+hp_status hp_nest_tune(hp_nest *n, const void *const *in_dev, void *out_dev, void *stream, int32_t flags);
+
 /* A-priori bound on the normalized error of each FP result of this nest
  * (|got - exact| / max(|exact|, scale), scale as reported by the tests):
  * 0 for integer precisions and MAX/MIN. */

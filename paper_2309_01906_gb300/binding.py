@@ -37,7 +37,7 @@ BODIES = {"load": HP_BODY_LOAD, "dot_bcast": HP_BODY_DOT_BCAST, "csr_gather": HP
 
 # every entry point include/hp.h declares
 EXPORTED = ["hp_nest_create", "hp_nest_run", "hp_nest_run_host", "hp_nest_run_static", "hp_nest_run_batch",
-            "hp_nest_error_bound",
+            "hp_nest_tune", "hp_nest_error_bound",
             "hp_nest_describe", "hp_nest_check", "hp_nest_destroy", "hp_serve_create", "hp_serve_submit",
             "hp_serve_poll", "hp_serve_stats", "hp_serve_destroy", "hp_set_option", "hp_get_option",
             "hp_last_error", "hp_version"]
@@ -92,6 +92,8 @@ def lib() -> ctypes.CDLL:
         L.hp_nest_run_static.argtypes = [p, p, p, p]
         L.hp_nest_run_batch.restype = i32
         L.hp_nest_run_batch.argtypes = [p, p, p, i32, p]
+        L.hp_nest_tune.restype = i32
+        L.hp_nest_tune.argtypes = [p, p, p, p, ctypes.c_int32]
         L.hp_nest_error_bound.restype = i32
         L.hp_nest_error_bound.argtypes = [p, ctypes.POINTER(ctypes.c_double)]
         L.hp_nest_describe.restype = i32
@@ -195,14 +197,42 @@ def hp_nest_run_static(nest, in_ptrs, out_ptr, stream=0):
     _check(st, "hp_nest_run_static")
 
 
-def hp_nest_run_batch(nests, in_ptr_lists, out_ptrs, stream=0):
-    n = len(nests)
-    harr = (ctypes.c_void_p * max(1, n))(*nests)
-    keep = [_ptr_array(x) for x in in_ptr_lists]
-    inarr = (ctypes.c_void_p * max(1, n))(*[ctypes.cast(k, ctypes.c_void_p) for k in keep])
-    outarr = _ptr_array(out_ptrs)
-    st = lib().hp_nest_run_batch(harr, inarr, outarr, n, stream or None)
+class PreparedBatch:
+    """Marshalled arguments of hp_nest_run_batch, built once and reused."""
+
+    def __init__(self, nests, in_ptr_lists, out_ptrs):
+        n = len(nests)
+        self.n = n
+        self.harr = (ctypes.c_void_p * max(1, n))(*nests)
+        self.keep = [_ptr_array(x) for x in in_ptr_lists]
+        self.inarr = (ctypes.c_void_p * max(1, n))(*[ctypes.cast(k, ctypes.c_void_p) for k in self.keep])
+        self.outarr = _ptr_array(out_ptrs)
+
+
+def hp_nest_run_batch(nests, in_ptr_lists=None, out_ptrs=None, stream=0):
+    """nests: list of handles (with in_ptr_lists, out_ptrs) or a PreparedBatch."""
+    pb = nests if isinstance(nests, PreparedBatch) else PreparedBatch(nests, in_ptr_lists, out_ptrs)
+    st = lib().hp_nest_run_batch(pb.harr, pb.inarr, pb.outarr, pb.n, stream or None)
     _check(st, "hp_nest_run_batch")
+
+
+class PreparedRun:
+    """Marshalled arguments of one hp_nest_run, built once and reused."""
+
+    def __init__(self, nest, in_ptrs, out_ptr):
+        self.nest = ctypes.c_void_p(nest)
+        self.inarr = _ptr_array(in_ptrs)
+        self.out = ctypes.c_void_p(out_ptr) if out_ptr else None
+
+    def __call__(self, stream=0):
+        st = lib().hp_nest_run(self.nest, self.inarr, self.out, stream or None)
+        _check(st, "hp_nest_run")
+
+
+def hp_nest_tune(nest, in_ptrs, out_ptr, stream=0, retime=False):
+    """Time candidate bindings on these buffers, install the fastest (synchronous)."""
+    st = lib().hp_nest_tune(nest, _ptr_array(in_ptrs), out_ptr or None, stream or None, 1 if retime else 0)
+    _check(st, "hp_nest_tune")
 
 
 def hp_nest_error_bound(nest) -> float:
@@ -284,6 +314,9 @@ class Nest:
 
     def run_host(self, in_ptrs, out_ptr, stream=0):
         hp_nest_run_host(self.handle, in_ptrs, out_ptr, stream)
+
+    def tune(self, in_ptrs, out_ptr, stream=0, retime=False):
+        hp_nest_tune(self.handle, in_ptrs, out_ptr, stream, retime)
 
     def describe(self) -> dict:
         return hp_nest_describe(self.handle)

@@ -16,6 +16,8 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
+
 #include <cuda_runtime.h>
 
 namespace hp {
@@ -227,6 +229,23 @@ __device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& 
   e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
 }
 
+// compensated fold of one value / one product into two slots at once
+__device__ __forceinline__ void comp_add_pair(float2& s, float2& c, float2 v) {
+  float2 t, e;
+  two_sum2(s, v, t, e);
+  s = t;
+  c = add2(c, e);
+}
+// the exact product errors come from two scalar FMAs (free operand negation)
+__device__ __forceinline__ void comp_prod_pair(float2& s, float2& c, float2 x, float2 w) {
+  const float2 p = mul2(x, w);
+  const float2 ep = make_float2(__fmaf_rn(x.x, w.x, -p.x), __fmaf_rn(x.y, w.y, -p.y));
+  float2 t, e;
+  two_sum2(s, p, t, e);
+  s = t;
+  c = add2(c, add2(ep, e));
+}
+
 // Fold state of the 4 vector slots of one thread.  The generic version uses
 // the policy's scalar operations; FP32 sums use packed pairs (slots 0,1 and
 // 2,3) with the same per-slot operation sequence, hence identical results.
@@ -261,28 +280,13 @@ template <>
 struct Fold4<OpF32Comp> {
   float2 s01, s23, c01, c23;   // leading and trailing words of slots (0,1) and (2,3)
   __device__ __forceinline__ void init() { s01 = s23 = c01 = c23 = make_float2(0.0f, 0.0f); }
-  __device__ __forceinline__ void add_pair(float2& s, float2& c, float2 v) {
-    float2 t, e;
-    two_sum2(s, v, t, e);
-    s = t;
-    c = add2(c, e);
-  }
   __device__ __forceinline__ void load(const float4& x) {
-    add_pair(s01, c01, make_float2(x.x, x.y));
-    add_pair(s23, c23, make_float2(x.z, x.w));
-  }
-  // the exact product errors come from two scalar FMAs (free operand negation)
-  __device__ __forceinline__ void prod_pair(float2& s, float2& c, float2 x, float2 w) {
-    const float2 p = mul2(x, w);
-    const float2 ep = make_float2(__fmaf_rn(x.x, w.x, -p.x), __fmaf_rn(x.y, w.y, -p.y));
-    float2 t, e;
-    two_sum2(s, p, t, e);
-    s = t;
-    c = add2(c, add2(ep, e));
+    comp_add_pair(s01, c01, make_float2(x.x, x.y));
+    comp_add_pair(s23, c23, make_float2(x.z, x.w));
   }
   __device__ __forceinline__ void dot(const float4& x, const float4& w, const float4&) {
-    prod_pair(s01, c01, make_float2(x.x, x.y), make_float2(w.x, w.y));
-    prod_pair(s23, c23, make_float2(x.z, x.w), make_float2(w.z, w.w));
+    comp_prod_pair(s01, c01, make_float2(x.x, x.y), make_float2(w.x, w.y));
+    comp_prod_pair(s23, c23, make_float2(x.z, x.w), make_float2(w.z, w.w));
   }
   __device__ __forceinline__ void get(f2 (&out)[4]) const {
     out[0] = {s01.x, c01.x};
@@ -311,5 +315,56 @@ struct Fold4<OpF32Sum> {
     out[3] = s23.y;
   }
 };
+
+// Fold V loaded values (and products with V broadcast values) into the V slot
+// accumulators acc[0..V-1]: slot i takes value i.  FP32 sums of 4 slots use the
+// packed pairs (0,1), (2,3); the per-slot operation sequence is unchanged.
+template <class Op, int V, class In>
+__device__ __forceinline__ void fold_vals_load(typename Op::Acc (&acc)[V], const In (&a)[V]) {
+  if constexpr (V == 4 && std::is_same<Op, OpF32Comp>::value) {
+    float2 s01 = make_float2(acc[0].s, acc[1].s), c01 = make_float2(acc[0].c, acc[1].c);
+    float2 s23 = make_float2(acc[2].s, acc[3].s), c23 = make_float2(acc[2].c, acc[3].c);
+    comp_add_pair(s01, c01, make_float2(a[0], a[1]));
+    comp_add_pair(s23, c23, make_float2(a[2], a[3]));
+    acc[0] = {s01.x, c01.x};
+    acc[1] = {s01.y, c01.y};
+    acc[2] = {s23.x, c23.x};
+    acc[3] = {s23.y, c23.y};
+  } else if constexpr (V == 4 && std::is_same<Op, OpF32Sum>::value) {
+    const float2 s01 = add2(make_float2(acc[0], acc[1]), make_float2(a[0], a[1]));
+    const float2 s23 = add2(make_float2(acc[2], acc[3]), make_float2(a[2], a[3]));
+    acc[0] = s01.x;
+    acc[1] = s01.y;
+    acc[2] = s23.x;
+    acc[3] = s23.y;
+  } else {
+#pragma unroll
+    for (int i = 0; i < V; ++i) Op::add_val(acc[i], a[i]);
+  }
+}
+
+template <class Op, int V, class In>
+__device__ __forceinline__ void fold_vals_dot(typename Op::Acc (&acc)[V], const In (&a)[V], const In (&b)[V]) {
+  if constexpr (V == 4 && std::is_same<Op, OpF32Comp>::value) {
+    float2 s01 = make_float2(acc[0].s, acc[1].s), c01 = make_float2(acc[0].c, acc[1].c);
+    float2 s23 = make_float2(acc[2].s, acc[3].s), c23 = make_float2(acc[2].c, acc[3].c);
+    comp_prod_pair(s01, c01, make_float2(a[0], a[1]), make_float2(b[0], b[1]));
+    comp_prod_pair(s23, c23, make_float2(a[2], a[3]), make_float2(b[2], b[3]));
+    acc[0] = {s01.x, c01.x};
+    acc[1] = {s01.y, c01.y};
+    acc[2] = {s23.x, c23.x};
+    acc[3] = {s23.y, c23.y};
+  } else if constexpr (V == 4 && std::is_same<Op, OpF32Sum>::value) {
+    const float2 s01 = fma2(make_float2(a[0], a[1]), make_float2(b[0], b[1]), make_float2(acc[0], acc[1]));
+    const float2 s23 = fma2(make_float2(a[2], a[3]), make_float2(b[2], b[3]), make_float2(acc[2], acc[3]));
+    acc[0] = s01.x;
+    acc[1] = s01.y;
+    acc[2] = s23.x;
+    acc[3] = s23.y;
+  } else {
+#pragma unroll
+    for (int i = 0; i < V; ++i) Op::add_prod(acc[i], a[i], b[i]);
+  }
+}
 
 }  // namespace hp

@@ -1,6 +1,7 @@
 // api.cu — the C ABI (include/hp.h): nest objects, device state, dispatch.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -13,6 +14,11 @@ using namespace hp;
 
 namespace hp {
 const std::string& last_error_string();
+
+uint64_t next_plan_id() {
+  static std::atomic<uint64_t> counter{0};
+  return ++counter;
+}
 
 hp_status ensure_device(hp_nest* n) {
   int dev = 0;
@@ -89,6 +95,22 @@ double error_bound(const hp_nest* n) {
   return 1e-6;
 }
 
+// free a rectangular nest's device scratch so that the next run re-plans its
+// launch and re-allocates for a new plan
+hp_status tune_release_device(hp_nest* n) {
+  if (n->device < 0) return HP_OK;
+  if (n->part) cudaFree(n->part);
+  if (n->geo) cudaFree(n->geo);
+  if (n->err) cudaFree(n->err);
+  n->part = nullptr;
+  n->geo = nullptr;
+  n->err = nullptr;
+  n->part_bytes = 0;
+  n->device = -1;
+  n->cfg = LaunchCfg();
+  return HP_OK;
+}
+
 size_t out_bytes(const hp_nest* n) {
   if (n->kind == NEST_RECT) return static_cast<size_t>(n->plan.rp.O) * n->plan.out_elem_bytes;
   return csr_out_bytes(n);
@@ -142,6 +164,7 @@ hp_status hp_nest_create(int depth, const int64_t* extents, const int64_t* csr_o
     delete n;
     return fail(st, why);
   }
+  n->plan_id = next_plan_id();
   *out = n;
   set_error("");
   return HP_OK;
@@ -236,6 +259,7 @@ hp_status hp_nest_check(hp_nest* n, void* stream, int32_t* device_error) {
 
 void hp_nest_destroy(hp_nest* n) {
   if (!n) return;
+  batch_forget(n);
   if (n->device >= 0) {
     if (n->part) cudaFree(n->part);
     if (n->geo) cudaFree(n->geo);

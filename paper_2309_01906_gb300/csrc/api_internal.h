@@ -28,9 +28,12 @@ struct hp_nest {
   void* stage_out = nullptr;
   size_t stage_out_bytes = 0;
   hp::CsrState* cs = nullptr; // CSR device state
+  uint64_t plan_id = 0;       // process-unique id of the current plan (new at create and when tuning replaces it)
 };
 
 namespace hp {
+uint64_t next_plan_id();
+void batch_forget(const hp_nest* n);   // drop cached batch contexts that contain n
 hp_status ensure_device(hp_nest* n);
 hp_status run_rect(hp_nest* n, const void* const* in_dev, void* out_dev, cudaStream_t st);
 size_t out_bytes(const hp_nest* n);

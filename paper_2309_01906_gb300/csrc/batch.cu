@@ -28,6 +28,7 @@ namespace {
 
 struct BatchCtx {
   std::vector<hp_nest*> key;
+  std::vector<uint64_t> ids;                   // plan id of each nest when built
   int device = -1;
   BatchNest* d_nests = nullptr;
   BatchNest* h_nests[2] = {nullptr, nullptr};   // pinned
@@ -45,6 +46,7 @@ struct BatchCtx {
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   cudaEvent_t done[2] = {nullptr, nullptr};
   bool used[2] = {false, false};
+  bool filled[2] = {false, false};   // plans written into pinned buffer b
   int parity = 0;
   int64_t n_tiles = 0;
 
@@ -185,6 +187,17 @@ hp_status build_ctx(BatchCtx& ctx, hp_nest* const* nests, int count, int dev, in
 
 }  // namespace
 
+// A destroyed nest's address can be reused by a new nest: drop every cached
+// context that refers to it.
+void batch_forget(const hp_nest* n) {
+  std::lock_guard<std::mutex> lock(g_batch_mu);
+  for (auto it = g_batch_ctx.begin(); it != g_batch_ctx.end();) {
+    const auto& key = (*it)->key;
+    if (std::find(key.begin(), key.end(), n) != key.end()) it = g_batch_ctx.erase(it);
+    else ++it;
+  }
+}
+
 }  // namespace hp
 
 using namespace hp;
@@ -218,8 +231,10 @@ extern "C" hp_status hp_nest_run_batch(hp_nest* const* nests, const void* const*
   // find (or build) the context of this exact list of nests
   BatchCtx* ctx = nullptr;
   for (auto it = g_batch_ctx.begin(); it != g_batch_ctx.end(); ++it) {
-    if ((*it)->device == dev && (*it)->key.size() == static_cast<size_t>(count) &&
-        std::equal((*it)->key.begin(), (*it)->key.end(), nests)) {
+    bool same = (*it)->device == dev && (*it)->key.size() == static_cast<size_t>(count) &&
+                std::equal((*it)->key.begin(), (*it)->key.end(), nests);
+    for (int i = 0; same && i < count; ++i) same = (*it)->ids[i] == nests[i]->plan_id;
+    if (same) {
       g_batch_ctx.splice(g_batch_ctx.begin(), g_batch_ctx, it);
       ctx = g_batch_ctx.front().get();
       break;
@@ -228,6 +243,7 @@ extern "C" hp_status hp_nest_run_batch(hp_nest* const* nests, const void* const*
   if (!ctx) {
     auto c = std::make_unique<BatchCtx>();
     c->key.assign(nests, nests + count);
+    for (int i = 0; i < count; ++i) c->ids.push_back(nests[i]->plan_id);
     hp_status st = build_ctx(*c, nests, count, dev, nests[0]->sms);
     if (st != HP_OK) return st;
     g_batch_ctx.push_front(std::move(c));
@@ -239,9 +255,10 @@ extern "C" hp_status hp_nest_run_batch(hp_nest* const* nests, const void* const*
   if (ctx->used[b] && (e = cudaEventSynchronize(ctx->done[b])) != cudaSuccess)
     return cuda_err(e, "wait for the previous use of the descriptor buffer");
   BatchNest* h = ctx->h_nests[b];
+  const bool first_fill = !ctx->filled[b];
   for (int i = 0; i < count; ++i) {
     const hp_nest* n = nests[i];
-    h[i].rp = n->plan.rp;
+    if (first_fill) h[i].rp = n->plan.rp;   // plans are fixed; later calls only rewrite the pointers
     h[i].in0 = n->plan.n_inputs > 0 ? in_dev[i][0] : nullptr;
     h[i].in1 = n->plan.n_inputs > 1 ? in_dev[i][1] : nullptr;
     h[i].out = out_dev[i];
@@ -252,6 +269,7 @@ extern "C" hp_status hp_nest_run_batch(hp_nest* const* nests, const void* const*
   if ((e = cudaGraphLaunch(ctx->exec[b], s)) != cudaSuccess) return cuda_err(e, "batch graph launch");
   if ((e = cudaEventRecord(ctx->done[b], s)) != cudaSuccess) return cuda_err(e, "batch event record");
   ctx->used[b] = true;
+  ctx->filled[b] = true;
   ctx->parity ^= 1;
   return HP_OK;
 }

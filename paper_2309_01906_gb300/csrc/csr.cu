@@ -547,10 +547,13 @@ inline hp_status cuda_fail(cudaError_t e, const char* what) {
   return fail(HP_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// the attribute belongs to the kernel (shared by every nest): always the
+// largest histogram any nest counts in shared memory
 template <class K>
 hp_status set_smem(K kernel, size_t dyn) {
   if (dyn == 0) return HP_OK;
-  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
+  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(kCsrHistSmemMax * sizeof(int)));
   return e == cudaSuccess ? HP_OK : cuda_fail(e, "CSR kernel shared memory");
 }
 

@@ -74,6 +74,7 @@ struct NestPlan {
   size_t out_elem_bytes = 4;
   std::vector<float> geo_table;      // GEOMETRIC body values fl32(q^k), k < m
   std::string kernel;                // name of the kernel family the plan runs
+  bool tuned = false;                // map taken from the tuning cache
 };
 
 // CSR plan (ragged 2-level nests).
@@ -97,6 +98,23 @@ struct LaunchCfg {
   int combine_grid = 0;
   int M = 1;           // items per round of a block team
 };
+
+// A tuned binding for a shape class (all reduced levels collapsed onto one
+// hardware level, outputs over the grid).
+struct TuneChoice {
+  int32_t red_hw = HP_HW_AUTO;  // hardware level of the reduced levels
+  int32_t sub = 0;              // SUBWARP width, LANE vector slots, or CTA warps
+  int64_t split_parts = 0;      // > 0: reduced levels split over this many grid parts
+};
+struct TuneKey {
+  int32_t lo, lr, vec, body, prec, op;
+  bool operator<(const TuneKey& o) const;
+};
+TuneKey tune_key(const NestPlan& p);
+bool tune_lookup(const TuneKey& k, TuneChoice* c);
+void tune_store(const TuneKey& k, const TuneChoice& c);
+void tune_apply(const NestPlan& p, const TuneChoice& c, hp_level_map* m);
+size_t tune_cache_size();
 
 // Validate a rectangular nest and build its plan.  Returns HP_OK or an error
 // with a message in *why.

@@ -19,7 +19,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <sstream>
+#include <tuple>
 
 #include "hp_internal.h"
 
@@ -55,6 +58,64 @@ hp_status fail(hp_status st, const std::string& msg) {
   return st;
 }
 const std::string& last_error_string() { return g_last_error; }
+
+namespace {
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneChoice> g_tune;
+
+int32_t ceil_log2(int64_t v) {
+  int32_t b = 0;
+  while ((int64_t(1) << b) < v && b < 62) ++b;
+  return b;
+}
+}  // namespace
+
+bool TuneKey::operator<(const TuneKey& o) const {
+  return std::tie(lo, lr, vec, body, prec, op) < std::tie(o.lo, o.lr, o.vec, o.body, o.prec, o.op);
+}
+
+// shape class: log2 buckets of outputs and reduced size, whether the reduced
+// block is a whole number of 128-bit groups, body, precision, operator
+TuneKey tune_key(const NestPlan& p) {
+  int64_t O = 1, R = 1;
+  for (int l = 0; l < p.red_level; ++l) O *= p.ext[l];
+  for (int l = p.red_level; l < p.depth; ++l) R *= p.ext[l];
+  return TuneKey{ceil_log2(O), ceil_log2(R), (R % 4 == 0) ? 1 : 0, static_cast<int32_t>(p.body),
+                 static_cast<int32_t>(p.prec), static_cast<int32_t>(p.op)};
+}
+
+bool tune_lookup(const TuneKey& k, TuneChoice* c) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tune.find(k);
+  if (it == g_tune.end()) return false;
+  *c = it->second;
+  return true;
+}
+
+void tune_store(const TuneKey& k, const TuneChoice& c) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[k] = c;
+}
+
+size_t tune_cache_size() {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  return g_tune.size();
+}
+
+// outputs over the grid; every reduced level on the chosen hardware level
+void tune_apply(const NestPlan& p, const TuneChoice& c, hp_level_map* m) {
+  const int d = p.depth, r = p.red_level;
+  int64_t R = 1;
+  for (int l = r; l < d; ++l) R *= p.ext[l];
+  for (int l = 0; l < d; ++l) m[l] = {HP_HW_GRID, 0, 0};
+  if (r == d) return;
+  if (c.split_parts > 0) {
+    const int64_t tile = std::max<int64_t>(1, (R + c.split_parts - 1) / c.split_parts);
+    for (int l = r; l < d; ++l) m[l] = {HP_HW_GRID, 0, l == r ? tile : 0};
+    return;
+  }
+  for (int l = r; l < d; ++l) m[l] = {c.red_hw, c.sub, 0};
+}
 
 static void auto_map(const NestPlan& p, hp_level_map* m) {
   const int d = p.depth, r = p.red_level;
@@ -157,7 +218,15 @@ hp_status plan_rect(int depth, const int64_t* extents, const hp_level_map* map, 
     if (any_auto && !all_auto) return bad("HP_HW_AUTO must be given for every level or for none");
   }
   p.auto_map = all_auto;
-  if (all_auto) auto_map(p, p.map);
+  if (all_auto) {
+    TuneChoice tc;
+    if (red_level < depth && tune_lookup(tune_key(p), &tc)) {
+      tune_apply(p, tc, p.map);
+      p.tuned = true;
+    } else {
+      auto_map(p, p.map);
+    }
+  }
   else
     for (int l = 0; l < depth; ++l) p.map[l] = map[l];
 
@@ -407,7 +476,8 @@ std::string describe_plan(const NestPlan& p) {
   for (int l = 0; l < p.depth; ++l)
     s << (l ? "," : "") << "{\"hw\":\"" << hw_name(p.map[l].hw) << "\",\"sub_width\":" << p.map[l].sub_width
       << ",\"tile\":" << p.map[l].tile << "}";
-  s << "],\"auto_map\":" << (p.auto_map ? "true" : "false") << ",\"team\":\"" << team_name(rp.team)
+  s << "],\"auto_map\":" << (p.auto_map ? "true" : "false") << ",\"tuned\":" << (p.tuned ? "true" : "false")
+    << ",\"team\":\"" << team_name(rp.team)
     << "\",\"outputs\":" << rp.O << ",\"reduced\":" << rp.R << ",\"items\":" << rp.items
     << ",\"cluster\":" << rp.C << ",\"warps\":" << rp.W << ",\"team_lanes\":" << rp.L
     << ",\"group_lanes\":" << rp.grp_lanes << ",\"vec\":" << rp.V << ",\"grid_parts\":" << rp.G

@@ -44,6 +44,15 @@ __device__ __forceinline__ auto v4get(const V4& v, int i) {
 
 // ---------------------------------------------------------------- bodies
 // fold V consecutive iterations starting at flat (reduced index rflat)
+// Memory bodies split a step into load (V consecutive iterations at flat, the
+// broadcast operand at rflat) and apply (fold them into the V slots), so that
+// fold_item can issue several loads before the first fold.
+template <class Op, int V>
+struct Vals {
+  typename Op::In a[V];
+  typename Op::In b[V];
+};
+
 template <class Op>
 struct BodyLoad {
   static constexpr bool kPipeable = true;
@@ -51,15 +60,27 @@ struct BodyLoad {
   const typename Op::In* A;
   __host__ __device__ const typename Op::In* wptr() const { return nullptr; }
   template <int V>
-  __device__ __forceinline__ void fold(typename Op::Acc (&acc)[V], int64_t flat, int64_t) const {
+  __device__ __forceinline__ Vals<Op, V> load(int64_t flat, int64_t) const {
+    Vals<Op, V> v;
     if constexpr (V == 4) {
-      const auto a = ld_stream4(A + flat);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) Op::add_val(acc[i], v4get(a, i));
+      const auto q = ld_stream4(A + flat);
+      v.a[0] = q.x;
+      v.a[1] = q.y;
+      v.a[2] = q.z;
+      v.a[3] = q.w;
     } else {
 #pragma unroll
-      for (int i = 0; i < V; ++i) Op::add_val(acc[i], ld_stream(A + flat + i));
+      for (int i = 0; i < V; ++i) v.a[i] = ld_stream(A + flat + i);
     }
+    return v;
+  }
+  template <int V>
+  __device__ __forceinline__ void apply(typename Op::Acc (&acc)[V], const Vals<Op, V>& v) const {
+    fold_vals_load<Op, V>(acc, v.a);
+  }
+  template <int V>
+  __device__ __forceinline__ void fold(typename Op::Acc (&acc)[V], int64_t flat, int64_t rflat) const {
+    apply<V>(acc, load<V>(flat, rflat));
   }
 };
 
@@ -71,16 +92,35 @@ struct BodyDot {
   const typename Op::In* w;
   __host__ __device__ const typename Op::In* wptr() const { return w; }
   template <int V>
-  __device__ __forceinline__ void fold(typename Op::Acc (&acc)[V], int64_t flat, int64_t rflat) const {
+  __device__ __forceinline__ Vals<Op, V> load(int64_t flat, int64_t rflat) const {
+    Vals<Op, V> v;
     if constexpr (V == 4) {
-      const auto a = ld_stream4(A + flat);
-      const auto b = ld_keep4(w + rflat);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) Op::add_prod(acc[i], v4get(a, i), v4get(b, i));
+      const auto q = ld_stream4(A + flat);
+      const auto r = ld_keep4(w + rflat);
+      v.a[0] = q.x;
+      v.a[1] = q.y;
+      v.a[2] = q.z;
+      v.a[3] = q.w;
+      v.b[0] = r.x;
+      v.b[1] = r.y;
+      v.b[2] = r.z;
+      v.b[3] = r.w;
     } else {
 #pragma unroll
-      for (int i = 0; i < V; ++i) Op::add_prod(acc[i], ld_stream(A + flat + i), ld_keep(w + rflat + i));
+      for (int i = 0; i < V; ++i) {
+        v.a[i] = ld_stream(A + flat + i);
+        v.b[i] = ld_keep(w + rflat + i);
+      }
     }
+    return v;
+  }
+  template <int V>
+  __device__ __forceinline__ void apply(typename Op::Acc (&acc)[V], const Vals<Op, V>& v) const {
+    fold_vals_dot<Op, V>(acc, v.a, v.b);
+  }
+  template <int V>
+  __device__ __forceinline__ void fold(typename Op::Acc (&acc)[V], int64_t flat, int64_t rflat) const {
+    apply<V>(acc, load<V>(flat, rflat));
   }
 };
 
@@ -152,8 +192,23 @@ __device__ __forceinline__ void fold_item(const RectPlan& p, const Body& body, i
     int64_t roff = 0;
     for (int v = 0; v < last; ++v) roff += x[v] * p.vstride[v];
     const int64_t base = obase + roff;
-#pragma unroll 4
-    for (int64_t xi = in_lo; xi < in_hi; xi += P) body.template fold<V>(acc, base + xi, roff + xi);
+    if constexpr (Body::kPipeable) {
+      // four loads in flight before the first of their folds (same fold order)
+      int64_t xi = in_lo;
+      for (; xi + 3 * P < in_hi; xi += 4 * P) {
+        const auto v0 = body.template load<V>(base + xi, roff + xi);
+        const auto v1 = body.template load<V>(base + xi + P, roff + xi + P);
+        const auto v2 = body.template load<V>(base + xi + 2 * P, roff + xi + 2 * P);
+        const auto v3 = body.template load<V>(base + xi + 3 * P, roff + xi + 3 * P);
+        body.template apply<V>(acc, v0);
+        body.template apply<V>(acc, v1);
+        body.template apply<V>(acc, v2);
+        body.template apply<V>(acc, v3);
+      }
+      for (; xi < in_hi; xi += P) body.template fold<V>(acc, base + xi, roff + xi);
+    } else {
+      for (int64_t xi = in_lo; xi < in_hi; xi += P) body.template fold<V>(acc, base + xi, roff + xi);
+    }
     int v = last - 1;
     for (; v >= 0; --v) {
       x[v] += p.vP[v];
@@ -446,6 +501,9 @@ __global__ void __launch_bounds__(kPipeMaxThreads, HP_PIPE_MIN_BLOCKS) rect_bloc
 
 // items in flight for a plan with G groups per item
 __host__ __device__ constexpr int pipe_depth(int groups) { return groups > 4 ? 2 : 4; }
+// largest dynamic shared memory of any pipelined plan: stages of 16-byte groups
+// for kPipeMaxThreads threads (D * G <= 16), or the pattern table
+constexpr size_t kPipeDynMax = static_cast<size_t>(kPipeMaxThreads) * 16 * 16;
 
 // ---------------------------------------------------------------- team = L lanes of a warp
 template <class Op, int V, class Body>

@@ -59,8 +59,11 @@ hp_status launch_team(const NestPlan& np, RectPlan rp, LaunchCfg& cfg, const Bod
   if (!cfg.ready) {
     cfg.threads = 32 * rp.W;
     cfg.cluster = block ? rp.C : 1;
-    if (dyn > 0) {  // static + dynamic shared memory may exceed the 48 KiB default
-      e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
+    if (pipe) {
+      // the attribute belongs to the kernel, not to this nest: always the
+      // largest size any plan of this kernel uses (static + dynamic may
+      // exceed the 48 KiB default)
+      e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kPipeDynMax));
       if (e != cudaSuccess) return cuda_fail(e, "dynamic shared memory size");
     }
     int per_sm = 0;

@@ -1,0 +1,149 @@
+// tune.cu — the autotuner: pick the level -> hardware binding of a nest's shape
+// class by timing legal candidates on the caller's buffers (Sec. 3.2 selects
+// levels by what they provide and Sec. 3.3 compiles a region for several
+// candidate levels and picks one at run time; here the pick is measured).
+//
+// Candidates keep the outputs on the grid and put every reduced level on one
+// hardware level: a CTA of 4 or 8 warps, a warp, a sub-warp group of 2..16
+// lanes, the 4 vector slots of one thread, one thread sequentially, or a split
+// of the reduction over several grid parts.  The winner is stored per shape
+// class (log2 of outputs and of the reduced size, 128-bit divisibility, body,
+// precision, operator); nests created later with an automatic map take it.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cfloat>
+#include <string>
+#include <vector>
+
+#include "api_internal.h"
+
+namespace hp {
+
+hp_status tune_release_device(hp_nest* n);
+
+namespace {
+
+std::vector<TuneChoice> candidates(const NestPlan& p, int sms) {
+  int64_t O = 1, R = 1;
+  for (int l = 0; l < p.red_level; ++l) O *= p.ext[l];
+  for (int l = p.red_level; l < p.depth; ++l) R *= p.ext[l];
+  std::vector<TuneChoice> c;
+  auto add = [&](int hw, int sub, int64_t parts) {
+    TuneChoice t;
+    t.red_hw = hw;
+    t.sub = sub;
+    t.split_parts = parts;
+    c.push_back(t);
+  };
+  if (R <= 64) add(HP_HW_SEQ, 0, 0);
+  if (R % 4 == 0 && R <= 256) add(HP_HW_LANE, 4, 0);
+  for (int w : {2, 4, 8, 16})
+    if (R >= 2 * w && R <= 256 * w) add(HP_HW_SUBWARP, w, 0);
+  if (R >= 32) add(HP_HW_WARP, 0, 0);
+  if (R >= 512) {
+    add(HP_HW_CTA, 4, 0);
+    add(HP_HW_CTA, 8, 0);
+  }
+  if (R >= 16384 && O < 8 * sms) {
+    for (int64_t want : {int64_t(sms), int64_t(2) * sms, int64_t(4) * sms}) {
+      const int64_t parts = std::max<int64_t>(2, (want + O - 1) / O);
+      if (R / parts >= 2048) add(HP_HW_GRID, 0, parts);
+    }
+  }
+  return c;
+}
+
+hp_status time_plan(hp_nest* tmp, const void* const* in_dev, void* out_dev, cudaStream_t st, float* ms) {
+  hp_status s = ensure_device(tmp);
+  if (s != HP_OK) return s;
+  if ((s = run_rect(tmp, in_dev, out_dev, st)) != HP_OK) return s;  // warm-up (and launch configuration)
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  constexpr int kReps = 3;
+  cudaEventRecord(e0, st);
+  for (int i = 0; i < kReps && s == HP_OK; ++i) s = run_rect(tmp, in_dev, out_dev, st);
+  cudaEventRecord(e1, st);
+  const cudaError_t e = cudaEventSynchronize(e1);
+  float t = 0.0f;
+  if (e == cudaSuccess) cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != HP_OK) return s;
+  if (e != cudaSuccess) return fail(HP_ECUDA, std::string("tuning run: ") + cudaGetErrorString(e));
+  *ms = t / kReps;
+  return HP_OK;
+}
+
+}  // namespace
+}  // namespace hp
+
+using namespace hp;
+
+extern "C" hp_status hp_nest_tune(hp_nest* n, const void* const* in_dev, void* out_dev, void* stream, int32_t flags) {
+  if (!n) return fail(HP_EINVAL, "nest is NULL");
+  if (n->kind != NEST_RECT) return fail(HP_EUNSUPPORTED, "only rectangular nests are tuned");
+  NestPlan& p = n->plan;
+  if (p.red_level == p.depth) return HP_OK;  // nothing is reduced: nothing to bind
+  hp_status s = ensure_device(n);
+  if (s != HP_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const TuneKey key = tune_key(p);
+  TuneChoice best;
+  const bool reuse = (flags & 1) == 0;
+  bool have = reuse && tune_lookup(key, &best);
+  if (!have) {
+    float best_ms = FLT_MAX;
+    const std::vector<TuneChoice> cand = candidates(p, n->sms);
+    for (const TuneChoice& c : cand) {
+      hp_level_map m[HP_MAX_DEPTH];
+      tune_apply(p, c, m);
+      hp_nest* tmp = nullptr;
+      const void* params = nullptr;
+      hp_affine_params ap;
+      if (p.body == HP_BODY_AFFINE) {
+        ap = {p.rp.aff_a, p.rp.aff_b, p.rp.aff_m};
+        params = &ap;
+      }
+      if (p.body == HP_BODY_GEOMETRIC) continue;  // table-driven test body: not tuned
+      if (hp_nest_create(p.depth, p.ext, nullptr, 0, m, p.op, p.red_level, p.prec, p.body, params, &tmp) != HP_OK)
+        continue;  // illegal for this shape
+      float ms = 0.0f;
+      const hp_status ts = time_plan(tmp, in_dev, out_dev, st, &ms);
+      hp_nest_destroy(tmp);
+      if (ts != HP_OK) {
+        if (ts == HP_ECUDA) return ts;
+        continue;
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = c;
+        have = true;
+      }
+    }
+    if (!have) return fail(HP_EUNSUPPORTED, "no candidate binding runs for this shape");
+    tune_store(key, best);
+  }
+  // install the winner in this nest (its device scratch is sized per plan)
+  hp_level_map m[HP_MAX_DEPTH];
+  tune_apply(p, best, m);
+  NestPlan np;
+  std::string why;
+  const void* params = nullptr;
+  hp_affine_params ap;
+  if (p.body == HP_BODY_AFFINE) {
+    ap = {p.rp.aff_a, p.rp.aff_b, p.rp.aff_m};
+    params = &ap;
+  }
+  s = plan_rect(p.depth, p.ext, m, p.op, p.red_level, p.prec, p.body, params, &np, &why);
+  if (s != HP_OK) return fail(s, why);
+  np.tuned = true;
+  s = tune_release_device(n);
+  if (s != HP_OK) return s;
+  n->plan = np;
+  n->plan_id = next_plan_id();   // cached batches built with the old plan no longer match
+  s = ensure_device(n);
+  if (s != HP_OK) return s;
+  return run_rect(n, in_dev, out_dev, st);  // the outputs hold the installed plan's result
+}

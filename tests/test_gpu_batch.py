@@ -116,3 +116,20 @@ def test_batch_rejects_cluster_teams():
         hb.hp_nest_run_batch([n.handle], [[0x1000]], [0x1000], 0)
     assert e.value.status == hb.HP_EUNSUPPORTED
     n.close()
+
+
+def test_batch_after_destroy_and_recreate():
+    # a destroyed nest's address may be reused by the next nest: the batch must
+    # be rebuilt for the new nest's plan, never replayed from the old one
+    import torch
+    rng = np.random.Generator(np.random.PCG64(406))
+    s = torch.cuda.current_stream().cuda_stream
+    for case in (MIXED[3], MIXED[14], MIXED[0], MIXED[6]):
+        it = _make(case, rng)
+        out = _out(it)
+        hb.hp_nest_run_batch([it["nest"].handle], [it["ins"]], [out.data_ptr()], s)
+        single = _out(it)
+        it["nest"].run(it["ins"], single.data_ptr(), s)
+        torch.cuda.synchronize()
+        assert torch.equal(out[:it["O"]], single[:it["O"]]), case
+        it["nest"].close()

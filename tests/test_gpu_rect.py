@@ -190,3 +190,15 @@ def test_four_level_workload_full_size():
     for prec in ("f32_comp", "f32"):
         got, _, bound = gpu_rect([64, 512, 16, 1024], 2, "sum", prec, "dot_bcast", lm, A=A, w=w)
         assert_close(got, ref, prec, "sum", bound, what=f"4-level full {prec}")
+
+
+def test_kernel_attributes_shared_between_nests():
+    # two nests on the same pipelined kernel with different shared-memory needs,
+    # the larger one first: its later runs must still launch
+    lm_a = [("grid", 0, 0), ("grid", 0, 0), ("cluster", 2, 0), ("cta", 8, 0)]   # 8 groups per thread
+    lm_b = [("grid", 0, 0), ("grid", 0, 0), ("cluster", 8, 0), ("cta", 8, 0)]   # 2 groups per thread
+    A, w = _inputs([3, 7, 16, 1024], 2, "f32_comp", "dot_bcast")
+    first = gpu_rect([3, 7, 16, 1024], 2, "sum", "f32_comp", "dot_bcast", lm_a, A=A, w=w)[0]
+    gpu_rect([3, 7, 16, 1024], 2, "sum", "f32_comp", "dot_bcast", lm_b, A=A, w=w)
+    again = gpu_rect([3, 7, 16, 1024], 2, "sum", "f32_comp", "dot_bcast", lm_a, A=A, w=w)[0]
+    assert np.array_equal(first, again)

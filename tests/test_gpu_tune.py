@@ -1,0 +1,50 @@
+"""GPU tests of the autotuner: candidates are timed on the caller's buffers, the
+winner is installed and cached per shape class, later automatic nests of the
+class take it, and results stay within the oracle tolerances."""
+import numpy as np
+import pytest
+
+from paper_2309_01906_gb300 import binding as hb
+from tests.hp_testutil import assert_close, oracle_rect
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("ext,r,op,prec", [([200, 3000], 1, "sum", "f32_comp"), ([5000, 6], 1, "max", "i32"),
+                                          ([3, 200000], 1, "sum", "f32"), ([64, 8, 100], 1, "sum", "i64")])
+def test_tune_installs_and_caches(ext, r, op, prec):
+    import torch
+    rng = np.random.Generator(np.random.PCG64(7))
+    total = int(np.prod(ext))
+    if prec in ("i32", "i64"):
+        A = rng.integers(-1000, 1001, total).astype(np.int32)
+        dt = torch.int32 if prec == "i32" else torch.int64
+    else:
+        A = rng.standard_normal(total).astype(np.float32)
+        dt = torch.float32
+    dA = torch.from_numpy(A).cuda()
+    O = int(np.prod(ext[:r]))
+    out = torch.empty(O, dtype=dt, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    n = hb.Nest(ext, r, op, prec, "load")
+    n.tune([dA.data_ptr()], out.data_ptr(), s, retime=True)
+    d = n.describe()
+    assert d["tuned"]
+    torch.cuda.synchronize()
+    ref = oracle_rect(ext, r, op, prec, "load", A=A)
+    assert_close(out.cpu().numpy(), ref, prec, op, n.error_bound(), what=f"tuned {ext}")
+    # a later automatic nest of the same shape class takes the cached binding
+    n2 = hb.Nest(ext, r, op, prec, "load")
+    d2 = n2.describe()
+    assert d2["tuned"] and d2["map"] == d["map"]
+    out2 = torch.empty(O, dtype=dt, device="cuda")
+    n2.run([dA.data_ptr()], out2.data_ptr(), s)
+    torch.cuda.synchronize()
+    assert torch.equal(out, out2)
+    # batching after tuning uses the installed plan
+    out3 = torch.empty(O, dtype=dt, device="cuda")
+    hb.hp_nest_run_batch([n.handle], [[dA.data_ptr()]], [out3.data_ptr()], s)
+    torch.cuda.synchronize()
+    assert torch.equal(out, out3)
+    n.close()
+    n2.close()
