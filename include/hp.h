@@ -263,11 +263,23 @@ hp_status hp_nest_check(hp_nest *n, void *stream, int32_t *device_error);
 void hp_nest_destroy(hp_nest *n);
 
 /* ---------------------------------------------------------------------- */
-/* Serving: continuous batching of nest requests under a device-memory budget. */
+/* Serving: continuous batching of nest requests under a device-memory budget.
+ *
+ * A scheduler thread admits submitted requests in arrival order while a slot
+ * is free and the admitted requests' inputs, outputs and grid-split scratch
+ * fit the budget, packs every admitted request that is not yet running into
+ * one step, and launches it on a free stream with the batched persistent
+ * kernels (so steps on different streams overlap, and requests arriving while
+ * others run join the next step).  A request runs its nest's own plan with the
+ * single-run reduction tree: its result is the same alone and in any mix, bit
+ * for bit.  With hp_set_option("serve_batching", 0) servers created afterwards
+ * launch every admitted request alone with the single-nest kernels (the plain
+ * per-request baseline).  Completion is observed on the host by event queries;
+ * no device code waits. */
 
 /* mem_budget_bytes: admission budget (inputs + outputs + scratch of admitted
- * requests); max_slots: requests resident at once; n_streams: CUDA streams the
- * scheduler launches steps on. */
+ * requests); max_slots: requests resident at once; n_streams (1..64): CUDA
+ * streams the scheduler launches steps on.  Needs a GPU (HP_ECUDA otherwise). */
 hp_status hp_serve_create(size_t mem_budget_bytes, int max_slots, int n_streams, hp_server **out);
 
 /* Submit one request: a nest (shape and plan; must stay alive until polled
@@ -285,6 +297,13 @@ hp_status hp_serve_poll(hp_server *s, uint64_t ticket, int timeout_us);
 hp_status hp_serve_stats(const hp_server *s, double *p50_us, double *p99_us, double *p999_us,
                          double *nests_per_s);
 
+/* Counters: completed requests, launched steps, peak admitted bytes and peak
+ * admitted requests (both stay within the budget and max_slots). */
+hp_status hp_serve_counters(const hp_server *s, uint64_t *completed, uint64_t *steps, size_t *peak_bytes,
+                            int32_t *peak_slots);
+
+/* Stops the scheduler after the steps in flight complete; requests still
+ * queued are dropped.  Nests and buffers stay the caller's. */
 void hp_serve_destroy(hp_server *s);
 
 /*
@@ -293,6 +312,8 @@ void hp_serve_destroy(hp_server *s);
  *   "pipeline"  1 (default): block teams whose element groups allow it stream
  *               their inputs through per-thread cp.async rings; 0: plain loads.
  *               Both give bit-identical results (same reduction tree).
+ *   "serve_batching"  1 (default): servers pack admitted requests into
+ *               batched steps; 0: servers launch each request alone.
  * HP_EINVAL for an unknown name.
  */
 hp_status hp_set_option(const char *name, int64_t value);

@@ -39,7 +39,7 @@ BODIES = {"load": HP_BODY_LOAD, "dot_bcast": HP_BODY_DOT_BCAST, "csr_gather": HP
 EXPORTED = ["hp_nest_create", "hp_nest_run", "hp_nest_run_host", "hp_nest_run_static", "hp_nest_run_batch",
             "hp_nest_tune", "hp_nest_error_bound",
             "hp_nest_describe", "hp_nest_check", "hp_nest_destroy", "hp_serve_create", "hp_serve_submit",
-            "hp_serve_poll", "hp_serve_stats", "hp_serve_destroy", "hp_set_option", "hp_get_option",
+            "hp_serve_poll", "hp_serve_stats", "hp_serve_counters", "hp_serve_destroy", "hp_set_option", "hp_get_option",
             "hp_last_error", "hp_version"]
 
 
@@ -110,6 +110,9 @@ def lib() -> ctypes.CDLL:
         L.hp_serve_poll.argtypes = [p, u64, i32]
         L.hp_serve_stats.restype = i32
         L.hp_serve_stats.argtypes = [p] + [ctypes.POINTER(ctypes.c_double)] * 4
+        L.hp_serve_counters.restype = i32
+        L.hp_serve_counters.argtypes = [p, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(ctypes.c_size_t),
+                                        ctypes.POINTER(ctypes.c_int32)]
         L.hp_serve_destroy.restype = None
         L.hp_serve_destroy.argtypes = [p]
         L.hp_last_error.restype = ctypes.c_char_p
@@ -285,6 +288,13 @@ def hp_serve_stats(server):
     v = [ctypes.c_double() for _ in range(4)]
     _check(lib().hp_serve_stats(server, *[ctypes.byref(x) for x in v]), "hp_serve_stats")
     return {"p50_us": v[0].value, "p99_us": v[1].value, "p999_us": v[2].value, "nests_per_s": v[3].value}
+
+
+def hp_serve_counters(server):
+    c, st, pb, ps = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_size_t(), ctypes.c_int32()
+    _check(lib().hp_serve_counters(server, ctypes.byref(c), ctypes.byref(st), ctypes.byref(pb), ctypes.byref(ps)),
+           "hp_serve_counters")
+    return {"completed": c.value, "steps": st.value, "peak_bytes": pb.value, "peak_slots": ps.value}
 
 
 def hp_serve_destroy(server):

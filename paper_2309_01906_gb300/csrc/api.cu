@@ -61,6 +61,11 @@ hp_status ensure_device(hp_nest* n) {
 }
 
 hp_status run_rect(hp_nest* n, const void* const* in_dev, void* out_dev, cudaStream_t st) {
+  return run_rect_with(n, in_dev, out_dev, n->part, st);
+}
+
+// run with caller-provided grid-part scratch (a server's per-request scratch)
+hp_status run_rect_with(hp_nest* n, const void* const* in_dev, void* out_dev, void* part, cudaStream_t st) {
   const NestPlan& p = n->plan;
   for (int i = 0; i < p.n_inputs; ++i) {
     if (!in_dev || !in_dev[i]) return fail(HP_EINVAL, "missing device input " + std::to_string(i));
@@ -68,7 +73,8 @@ hp_status run_rect(hp_nest* n, const void* const* in_dev, void* out_dev, cudaStr
       return fail(HP_EINVAL, "input " + std::to_string(i) + " must be 16-byte aligned (plan uses 128-bit loads)");
   }
   if (!out_dev && p.rp.O > 0) return fail(HP_EINVAL, "out_dev is NULL");
-  RectArgs a{in_dev, out_dev, n->part, n->geo, st};
+  if (p.rp.G > 1 && p.rp.items > 0 && !part) return fail(HP_EINVAL, "grid-split plan without partial scratch");
+  RectArgs a{in_dev, out_dev, part, n->geo, st};
   const bool fp = p.prec == HP_F32 || p.prec == HP_F32_COMP;
   switch (p.op) {
     case HP_RED_SUM:
@@ -129,6 +135,10 @@ hp_status hp_set_option(const char* name, int64_t value) {
     options().pipeline = value;
     return HP_OK;
   }
+  if (n == "serve_batching") {
+    options().serve_batching = value;
+    return HP_OK;
+  }
   return fail(HP_EINVAL, "unknown option " + n);
 }
 
@@ -137,6 +147,10 @@ hp_status hp_get_option(const char* name, int64_t* value) {
   const std::string n(name);
   if (n == "pipeline") {
     *value = options().pipeline;
+    return HP_OK;
+  }
+  if (n == "serve_batching") {
+    *value = options().serve_batching;
     return HP_OK;
   }
   return fail(HP_EINVAL, "unknown option " + n);

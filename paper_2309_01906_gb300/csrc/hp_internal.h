@@ -129,6 +129,7 @@ double error_bound_rect(const NestPlan& p);
 // Process-wide options read when a nest is planned (hp_set_option).
 struct Options {
   int64_t pipeline = 1;    // allow the cp.async-pipelined block kernel
+  int64_t serve_batching = 1;  // servers created now pack admitted requests into batched steps
 };
 Options& options();
 

@@ -1,0 +1,514 @@
+// serve.cu — continuous batching of nest requests under a device-memory budget.
+//
+// A scheduler thread owns the GPU side of a server.  Submitted requests wait in
+// a queue; the scheduler admits them while a slot is free and the admitted
+// requests' inputs, outputs and scratch stay within the budget, packs every
+// admitted request that is not yet running into one step, and launches the step
+// on a free stream with the batched persistent kernels (one per arithmetic).
+// With several streams, steps overlap on the device and requests that arrive
+// while others run join the next step.  Completion is observed by querying the
+// step's event; the scheduler then frees the slots, memory and scratch and
+// admits more.  No device code waits on anything.
+//
+// Every request runs its nest's own plan with the single-run reduction tree
+// (the batched kernels are bit-identical to hp_nest_run), so a result does not
+// depend on what else was in its step.  Grid-split plans take their partials
+// and tickets from server-owned pools, so concurrent requests on one nest never
+// share scratch.  With hp_set_option("serve_batching", 0) a server launches
+// every request alone with the single-nest kernels instead (the plain
+// per-request baseline).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "api_internal.h"
+#include "batch_kernels.cuh"
+#include "rect_launch.cuh"
+
+namespace hp {
+
+hp_status run_rect_with(hp_nest* n, const void* const* in_dev, void* out_dev, void* part, cudaStream_t st);
+const std::string& last_error_string();
+
+namespace {
+
+double now_us() {
+  return std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// first-fit allocator of byte ranges inside one device block
+class RangeAlloc {
+ public:
+  void reset(size_t cap) {
+    free_.clear();
+    if (cap) free_[0] = cap;
+  }
+  bool alloc(size_t n, size_t* off) {
+    n = (n + 255) & ~size_t(255);
+    if (n == 0) {
+      *off = 0;
+      return true;
+    }
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= n) {
+        *off = it->first;
+        const size_t rest = it->second - n, start = it->first + n;
+        free_.erase(it);
+        if (rest) free_[start] = rest;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t n) {
+    n = (n + 255) & ~size_t(255);
+    if (n == 0) return;
+    auto it = free_.emplace(off, n).first;
+    auto next = std::next(it);
+    if (next != free_.end() && it->first + it->second == next->first) {
+      it->second += next->second;
+      free_.erase(next);
+    }
+    if (it != free_.begin()) {
+      auto prev = std::prev(it);
+      if (prev->first + prev->second == it->first) {
+        prev->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+
+ private:
+  std::map<size_t, size_t> free_;
+};
+
+enum ReqState : uint8_t { RQ_QUEUED = 0, RQ_RUNNING = 1, RQ_DONE = 2, RQ_FAILED = 3 };
+
+struct Request {
+  uint64_t ticket;
+  hp_nest* nest;
+  const void* in[2];
+  void* out;
+  double t_submit;
+  size_t bytes;          // inputs + outputs + scratch counted against the budget
+  size_t part_bytes, ticket_bytes;
+  size_t part_off, ticket_off;
+  uint8_t state;
+};
+
+struct Step {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  bool busy = false;
+  std::vector<Request*> reqs;     // admitted into this step (stable deque elements)
+  BatchNest* h_nests = nullptr;   // pinned staging
+  BatchTile* h_tiles = nullptr;
+  size_t cap_nests = 0, cap_tiles = 0;      // pinned capacities
+  BatchNest* d_nests = nullptr;
+  BatchTile* d_tiles = nullptr;
+  size_t dcap_nests = 0, dcap_tiles = 0;    // device capacities
+  unsigned long long* d_counters = nullptr;
+};
+
+}  // namespace
+}  // namespace hp
+
+struct hp_server {
+  size_t budget = 0;
+  int max_slots = 0;
+  int max_step = 4096;               // requests per step
+  bool batching = true;
+  int device = 0, sms = 0;
+  std::mutex mu;
+  std::condition_variable cv_done;
+  std::deque<uint64_t> queue;
+  std::deque<hp::Request> reqs;      // ticket t is reqs[t - 1]; elements never move
+  size_t bytes_in_flight = 0;
+  int slots_used = 0;
+  std::vector<hp::Step> steps;
+  // scratch pools of grid-split plans
+  void* part_pool = nullptr;
+  int32_t* ticket_pool = nullptr;    // kept all-zero between uses
+  size_t part_cap = 0, ticket_cap = 0;
+  hp::RangeAlloc part_alloc, ticket_alloc;
+  // statistics
+  std::vector<double> lat_us;
+  double t_first = 0.0, t_last = 0.0;
+  uint64_t n_done = 0;
+  uint64_t n_steps = 0;
+  size_t peak_bytes = 0;
+  int peak_slots = 0;
+  std::string error;
+  std::atomic<bool> stop{false};
+  std::thread th;
+};
+
+namespace hp {
+namespace {
+
+size_t request_bytes(const hp_nest* n, size_t* part_bytes, size_t* ticket_bytes) {
+  const NestPlan& p = n->plan;
+  const RectPlan& rp = p.rp;
+  size_t b = 0;
+  for (int i = 0; i < p.n_inputs; ++i) b += static_cast<size_t>(p.in_elems[i]) * p.in_elem_bytes;
+  b += static_cast<size_t>(rp.O) * p.out_elem_bytes;
+  *part_bytes = rp.G > 1 ? static_cast<size_t>(rp.items) * partial_bytes(p.prec, p.op) : 0;
+  *ticket_bytes = rp.G > 1 ? static_cast<size_t>(rp.O) * sizeof(int32_t) : 0;
+  return b + *part_bytes + *ticket_bytes;
+}
+
+// tiles of one request's nest (work items cut into ranges of about `target` elements)
+void step_tiles(int nest, const RectPlan& rp, int64_t target, std::vector<BatchTile>& out) {
+  if (rp.items == 0) return;
+  int64_t per_item = rp.team == TEAM_MAP ? 1
+                   : rp.split ? std::max<int64_t>(1, rp.R / std::max<int64_t>(1, rp.vn[0]) * rp.tile)
+                              : std::max<int64_t>(1, rp.R);
+  int64_t k = std::max<int64_t>(1, target / per_item);
+  if (rp.team == TEAM_LANES) {
+    const int64_t teams = (kBatchThreads / 32) * (32 / rp.L);
+    k = (k + teams - 1) / teams * teams;
+  }
+  if (rp.team == TEAM_MAP) k = std::max<int64_t>(k, kBatchThreads);
+  k = std::min<int64_t>(k, int64_t(1) << 30);
+  for (int64_t i0 = 0; i0 < rp.items; i0 += k)
+    out.push_back({nest, static_cast<int32_t>(std::min<int64_t>(k, rp.items - i0)), i0});
+}
+
+}  // namespace
+}  // namespace hp
+
+namespace hp {
+namespace {
+
+bool grow_pinned(void** p, size_t* cap, size_t need, size_t elem) {
+  if (*cap >= need) return true;
+  size_t n = std::max(need, *cap * 2 + 64);
+  if (*p) cudaFreeHost(*p);
+  *p = nullptr;
+  *cap = 0;
+  if (cudaMallocHost(p, n * elem) != cudaSuccess) return false;
+  *cap = n;
+  return true;
+}
+
+bool grow_device(void** p, size_t* cap, size_t need, size_t elem) {
+  if (*cap >= need) return true;
+  size_t n = std::max(need, *cap * 2 + 64);
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  if (cudaMalloc(p, n * elem) != cudaSuccess) return false;
+  *cap = n;
+  return true;
+}
+
+// launch one step: all its requests in one persistent kernel per arithmetic
+hp_status launch_batched(hp_server* s, Step& st) {
+  const size_t n = st.reqs.size();
+  std::vector<BatchTile> tiles[kBatchCombos];
+  int64_t total = 0;
+  for (const Request* r : st.reqs) {
+    const RectPlan& rp = r->nest->plan.rp;
+    total += rp.team == TEAM_MAP ? rp.O : rp.O * std::max<int64_t>(1, rp.R);
+  }
+  const int64_t target = std::max<int64_t>(1 << 14, total / (4 * static_cast<int64_t>(s->sms) * 8));
+  if (!grow_pinned(reinterpret_cast<void**>(&st.h_nests), &st.cap_nests, n, sizeof(BatchNest)))
+    return fail(HP_ENOMEM, "pinned step descriptors");
+  for (size_t i = 0; i < n; ++i) {
+    const Request& r = *st.reqs[i];
+    const NestPlan& p = r.nest->plan;
+    BatchNest& bn = st.h_nests[i];
+    bn.rp = p.rp;
+    bn.in0 = r.in[0];
+    bn.in1 = r.in[1];
+    bn.out = r.out;
+    bn.part = r.part_bytes ? static_cast<char*>(s->part_pool) + r.part_off : nullptr;
+    bn.tickets = r.ticket_bytes ? reinterpret_cast<int32_t*>(reinterpret_cast<char*>(s->ticket_pool) + r.ticket_off)
+                                : nullptr;
+    step_tiles(static_cast<int>(i), p.rp, target, tiles[batch_combo(p.prec, p.op)]);
+  }
+  size_t n_tiles = 0;
+  for (auto& v : tiles) n_tiles += v.size();
+  if (!grow_pinned(reinterpret_cast<void**>(&st.h_tiles), &st.cap_tiles, n_tiles, sizeof(BatchTile)))
+    return fail(HP_ENOMEM, "pinned step tiles");
+  if (!grow_device(reinterpret_cast<void**>(&st.d_nests), &st.dcap_nests, n, sizeof(BatchNest)) ||
+      !grow_device(reinterpret_cast<void**>(&st.d_tiles), &st.dcap_tiles, n_tiles, sizeof(BatchTile)))
+    return fail(HP_ENOMEM, "device step tables");
+  size_t off = 0;
+  int64_t first[kBatchCombos];
+  for (int c = 0; c < kBatchCombos; ++c) {
+    first[c] = static_cast<int64_t>(off);
+    std::copy(tiles[c].begin(), tiles[c].end(), st.h_tiles + off);
+    off += tiles[c].size();
+  }
+  cudaError_t e = cudaMemcpyAsync(st.d_nests, st.h_nests, n * sizeof(BatchNest), cudaMemcpyHostToDevice, st.stream);
+  if (e == cudaSuccess && n_tiles)
+    e = cudaMemcpyAsync(st.d_tiles, st.h_tiles, n_tiles * sizeof(BatchTile), cudaMemcpyHostToDevice, st.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(st.d_counters, 0, kBatchCombos * sizeof(unsigned long long), st.stream);
+  for (int c = 0; e == cudaSuccess && c < kBatchCombos; ++c) {
+    if (tiles[c].empty()) continue;
+    const int grid = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(tiles[c].size()),
+                                                        static_cast<int64_t>(batch_combo_blocks_per_sm(c)) * s->sms));
+    BatchLaunch L{st.d_nests, st.d_tiles + first[c], static_cast<int64_t>(tiles[c].size()), st.d_counters + c, grid};
+    e = launch_batch_combo(c, L, st.stream);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(st.done, st.stream);
+  if (e != cudaSuccess) return fail(HP_ECUDA, std::string("serve step launch: ") + cudaGetErrorString(e));
+  return HP_OK;
+}
+
+// plain mode: every request of the step launched alone with the single-nest kernels
+hp_status launch_plain(hp_server* s, Step& st) {
+  for (Request* r : st.reqs) {
+    void* part = r->part_bytes ? static_cast<char*>(s->part_pool) + r->part_off : nullptr;
+    const hp_status h = run_rect_with(r->nest, r->in, r->out, part, st.stream);
+    if (h != HP_OK) return h;
+  }
+  const cudaError_t e = cudaEventRecord(st.done, st.stream);
+  return e == cudaSuccess ? HP_OK : fail(HP_ECUDA, "serve event record");
+}
+
+void finish_step(hp_server* s, Step& st, bool ok) {
+  const double t = now_us();
+  std::lock_guard<std::mutex> lock(s->mu);
+  for (Request* r : st.reqs) {
+    r->state = ok ? RQ_DONE : RQ_FAILED;
+    s->bytes_in_flight -= r->bytes;
+    s->slots_used -= 1;
+    if (r->part_bytes) s->part_alloc.release(r->part_off, r->part_bytes);
+    if (r->ticket_bytes) s->ticket_alloc.release(r->ticket_off, r->ticket_bytes);
+    if (ok) {
+      s->lat_us.push_back(t - r->t_submit);
+      s->n_done += 1;
+      s->t_last = t;
+    }
+  }
+  st.reqs.clear();
+  st.busy = false;
+  s->cv_done.notify_all();
+}
+
+void scheduler(hp_server* s) {
+  cudaSetDevice(s->device);
+  while (!s->stop.load(std::memory_order_relaxed)) {
+    bool progress = false;
+    for (Step& st : s->steps) {
+      if (!st.busy) continue;
+      const cudaError_t q = cudaEventQuery(st.done);
+      if (q == cudaSuccess || q != cudaErrorNotReady) {
+        if (q != cudaSuccess) {
+          std::lock_guard<std::mutex> lock(s->mu);
+          s->error = std::string("step failed: ") + cudaGetErrorString(q);
+        }
+        finish_step(s, st, q == cudaSuccess);
+        progress = true;
+      }
+    }
+    for (Step& st : s->steps) {
+      if (st.busy) continue;
+      {
+        // admit queued requests while a slot, the budget and scratch allow
+        std::lock_guard<std::mutex> lock(s->mu);
+        while (!s->queue.empty() && s->slots_used < s->max_slots &&
+               static_cast<int>(st.reqs.size()) < s->max_step) {
+          Request& r = s->reqs[s->queue.front() - 1];
+          if (s->bytes_in_flight + r.bytes > s->budget) break;
+          if (r.part_bytes && !s->part_alloc.alloc(r.part_bytes, &r.part_off)) break;
+          if (r.ticket_bytes && !s->ticket_alloc.alloc(r.ticket_bytes, &r.ticket_off)) {
+            if (r.part_bytes) s->part_alloc.release(r.part_off, r.part_bytes);
+            break;
+          }
+          s->queue.pop_front();
+          s->bytes_in_flight += r.bytes;
+          s->slots_used += 1;
+          s->peak_bytes = std::max(s->peak_bytes, s->bytes_in_flight);
+          s->peak_slots = std::max(s->peak_slots, s->slots_used);
+          r.state = RQ_RUNNING;
+          st.reqs.push_back(&r);
+        }
+      }
+      if (st.reqs.empty()) break;
+      const hp_status h = s->batching ? launch_batched(s, st) : launch_plain(s, st);
+      if (h != HP_OK) {
+        {
+          std::lock_guard<std::mutex> lock(s->mu);
+          s->error = last_error_string();
+        }
+        finish_step(s, st, false);
+      } else {
+        st.busy = true;
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->n_steps += 1;
+      }
+      progress = true;
+    }
+    if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(5));
+  }
+}
+
+}  // namespace
+}  // namespace hp
+
+using namespace hp;
+
+extern "C" {
+
+hp_status hp_serve_create(size_t mem_budget_bytes, int max_slots, int n_streams, hp_server** out) {
+  if (!out) return fail(HP_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (mem_budget_bytes == 0 || max_slots < 1 || n_streams < 1 || n_streams > 64)
+    return fail(HP_EINVAL, "budget must be > 0, max_slots >= 1, n_streams in [1, 64]");
+  hp_server* s = new (std::nothrow) hp_server();
+  if (!s) return fail(HP_ENOMEM, "host allocation failed");
+  s->budget = mem_budget_bytes;
+  s->max_slots = max_slots;
+  s->batching = options().serve_batching != 0;
+  cudaError_t e = cudaGetDevice(&s->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
+  if (e != cudaSuccess) {
+    delete s;
+    return fail(HP_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  }
+  // scratch pools for grid-split plans: partials and (always zero) tickets
+  s->part_cap = std::min<size_t>(mem_budget_bytes / 8 + (1 << 20), size_t(1) << 30);
+  s->ticket_cap = std::min<size_t>(mem_budget_bytes / 64 + (1 << 20), size_t(64) << 20);
+  if (cudaMalloc(&s->part_pool, s->part_cap) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void**>(&s->ticket_pool), s->ticket_cap) != cudaSuccess ||
+      cudaMemset(s->ticket_pool, 0, s->ticket_cap) != cudaSuccess) {
+    hp_serve_destroy(s);
+    return fail(HP_ENOMEM, "cudaMalloc (serving scratch pools)");
+  }
+  s->part_alloc.reset(s->part_cap);
+  s->ticket_alloc.reset(s->ticket_cap);
+  s->steps.resize(n_streams);
+  for (Step& st : s->steps) {
+    if (cudaStreamCreateWithFlags(&st.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&st.done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMalloc(&st.d_counters, kBatchCombos * sizeof(unsigned long long)) != cudaSuccess) {
+      hp_serve_destroy(s);
+      return fail(HP_ECUDA, "serving streams");
+    }
+  }
+  s->th = std::thread(scheduler, s);
+  *out = s;
+  return HP_OK;
+}
+
+hp_status hp_serve_submit(hp_server* s, const hp_nest* shape, const void* const* in_dev, void* out_dev,
+                          uint64_t* ticket) {
+  if (!s || !shape || !ticket) return fail(HP_EINVAL, "NULL argument");
+  hp_nest* n = const_cast<hp_nest*>(shape);
+  if (n->kind != NEST_RECT) return fail(HP_EUNSUPPORTED, "served nests must be rectangular");
+  const RectPlan& rp = n->plan.rp;
+  if (s->batching && rp.team == TEAM_BLOCK && (rp.C > 1 || rp.W > kBatchThreads / 32))
+    return fail(HP_EUNSUPPORTED, "served block teams are single CTAs of at most 8 warps");
+  if (n->plan.body == HP_BODY_GEOMETRIC) return fail(HP_EUNSUPPORTED, "the GEOMETRIC body is not served");
+  hp_status st = ensure_device(n);
+  if (st != HP_OK) return st;
+  for (int i = 0; i < n->plan.n_inputs; ++i)
+    if (!in_dev || !in_dev[i]) return fail(HP_EINVAL, "missing device input");
+  if (!out_dev && rp.O > 0) return fail(HP_EINVAL, "out_dev is NULL");
+  Request r{};
+  r.nest = n;
+  r.in[0] = n->plan.n_inputs > 0 ? in_dev[0] : nullptr;
+  r.in[1] = n->plan.n_inputs > 1 ? in_dev[1] : nullptr;
+  r.out = out_dev;
+  r.bytes = request_bytes(n, &r.part_bytes, &r.ticket_bytes);
+  if (r.bytes > s->budget) return fail(HP_ENOMEM, "request alone exceeds the server's memory budget");
+  if (r.part_bytes > s->part_cap || r.ticket_bytes > s->ticket_cap)
+    return fail(HP_ENOMEM, "request's grid-split scratch exceeds the server's scratch pool");
+  r.state = RQ_QUEUED;
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (!s->error.empty()) return fail(HP_ECUDA, s->error);
+  r.t_submit = now_us();
+  if (s->reqs.empty()) s->t_first = r.t_submit;
+  r.ticket = s->reqs.size() + 1;
+  s->reqs.push_back(r);
+  *ticket = r.ticket;
+  s->queue.push_back(*ticket);
+  return HP_OK;
+}
+
+hp_status hp_serve_poll(hp_server* s, uint64_t ticket, int timeout_us) {
+  if (!s) return fail(HP_EINVAL, "server is NULL");
+  std::unique_lock<std::mutex> lock(s->mu);
+  if (ticket == 0 || ticket > s->reqs.size()) return fail(HP_EINVAL, "unknown ticket");
+  auto state = [&] { return s->reqs[ticket - 1].state; };
+  if (state() < RQ_DONE && timeout_us != 0) {
+    auto done = [&] { return state() >= RQ_DONE; };
+    if (timeout_us < 0) s->cv_done.wait(lock, done);
+    else s->cv_done.wait_for(lock, std::chrono::microseconds(timeout_us), done);
+  }
+  const uint8_t st = state();
+  if (st == RQ_DONE) return HP_OK;
+  if (st == RQ_FAILED) return fail(HP_ECUDA, "request failed: " + s->error);
+  return timeout_us == 0 ? HP_EAGAIN : HP_ETIMEOUT;
+}
+
+hp_status hp_serve_stats(const hp_server* cs, double* p50, double* p99, double* p999, double* nps) {
+  if (!cs) return fail(HP_EINVAL, "server is NULL");
+  hp_server* s = const_cast<hp_server*>(cs);
+  std::vector<double> v;
+  double t0, t1;
+  uint64_t n;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    v = s->lat_us;
+    t0 = s->t_first;
+    t1 = s->t_last;
+    n = s->n_done;
+  }
+  auto pct = [&](double q) {
+    if (v.empty()) return 0.0;
+    const size_t k = std::min(v.size() - 1, static_cast<size_t>(q * static_cast<double>(v.size() - 1) + 0.5));
+    std::nth_element(v.begin(), v.begin() + static_cast<long>(k), v.end());
+    return v[k];
+  };
+  if (p50) *p50 = pct(0.5);
+  if (p99) *p99 = pct(0.99);
+  if (p999) *p999 = pct(0.999);
+  if (nps) *nps = (n > 0 && t1 > t0) ? static_cast<double>(n) / ((t1 - t0) * 1e-6) : 0.0;
+  return HP_OK;
+}
+
+hp_status hp_serve_counters(const hp_server* cs, uint64_t* completed, uint64_t* steps, size_t* peak_bytes,
+                            int32_t* peak_slots) {
+  if (!cs) return fail(HP_EINVAL, "server is NULL");
+  hp_server* s = const_cast<hp_server*>(cs);
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (completed) *completed = s->n_done;
+  if (steps) *steps = s->n_steps;
+  if (peak_bytes) *peak_bytes = s->peak_bytes;
+  if (peak_slots) *peak_slots = s->peak_slots;
+  return HP_OK;
+}
+
+void hp_serve_destroy(hp_server* s) {
+  if (!s) return;
+  s->stop.store(true);
+  if (s->th.joinable()) s->th.join();
+  for (Step& st : s->steps) {
+    if (st.stream) cudaStreamSynchronize(st.stream);
+    if (st.done) cudaEventDestroy(st.done);
+    if (st.stream) cudaStreamDestroy(st.stream);
+    if (st.h_nests) cudaFreeHost(st.h_nests);
+    if (st.h_tiles) cudaFreeHost(st.h_tiles);
+    if (st.d_nests) cudaFree(st.d_nests);
+    if (st.d_tiles) cudaFree(st.d_tiles);
+    if (st.d_counters) cudaFree(st.d_counters);
+  }
+  if (s->part_pool) cudaFree(s->part_pool);
+  if (s->ticket_pool) cudaFree(s->ticket_pool);
+  delete s;
+}
+
+}  // extern "C"

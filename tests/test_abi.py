@@ -143,3 +143,16 @@ def test_run_without_gpu_fails_loudly():
     e = _err(n.run, [], 0x1000, 0)
     assert e.status == hb.HP_ECUDA
     n.close()
+
+
+def test_serving_needs_a_gpu():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    e = _err(hb.hp_serve_create, 1 << 30, 8, 2)
+    assert e.status == hb.HP_ECUDA
+    e = _err(hb.hp_serve_create, 0, 8, 2)
+    assert e.status == hb.HP_EINVAL
+    hb.hp_set_option("serve_batching", 0)
+    assert hb.hp_get_option("serve_batching") == 0
+    hb.hp_set_option("serve_batching", 1)
