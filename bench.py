@@ -569,6 +569,72 @@ def run_batch_workload(args):
         nest.close()
 
 
+def run_serve_workload(args):
+    """Serving: a Poisson stream of nest requests (seed 10) at --serve-rate for
+    --serve-seconds; shapes drawn as in the batched workload (seed 9), all FP32
+    compensated sums over pre-generated device inputs; 40 GiB admission budget.
+    The same arrival sequence is served by the batched server and by the plain
+    per-request server; latency is submission to observed completion."""
+    import torch
+
+    from paper_2309_01906_gb300 import binding as hb
+    from paper_2309_01906_gb300 import synth
+    n_pool = args.serve_pool
+    shapes = synth.uneven_shapes(n_nests=n_pool, seed=9, sum_prec="f32_comp")
+    pool = []
+    for i, sh in enumerate(shapes):
+        A = synth.normal_f32(sh.size, 9, 1 + i)
+        n = hb.Nest(list(sh.extents), sh.red_level, "sum", "f32_comp", "load")
+        outs = [torch.empty(max(sh.n_out, 1), dtype=torch.float32, device="cuda") for _ in range(4)]
+        pool.append((n, torch.from_numpy(A).cuda(), outs, sh))
+    arrivals = synth.poisson_arrivals(rate=args.serve_rate, duration=args.serve_seconds, seed=10)
+    pick = np.random.Generator(np.random.PCG64(np.random.SeedSequence(10, spawn_key=(1,)))).integers(
+        0, n_pool, arrivals.size)
+    iters = float(np.mean([pool[k][3].size for k in pick]))
+
+    def serve(batching):
+        hb.hp_set_option("serve_batching", 1 if batching else 0)
+        try:
+            server = hb.hp_serve_create(40 << 30, 4096, 4)
+        finally:
+            hb.hp_set_option("serve_batching", 1)
+        use = [0] * n_pool
+        lag = 0.0
+        t0 = time.perf_counter()
+        last = 0
+        for j, t_arr in enumerate(arrivals):
+            while True:
+                now = time.perf_counter() - t0
+                if now >= t_arr:
+                    break
+            lag = max(lag, now - t_arr)
+            n, dA, outs, _ = pool[pick[j]]
+            out = outs[use[pick[j]] % 4]
+            use[pick[j]] += 1
+            last = hb.hp_serve_submit(server, n.handle, [dA.data_ptr()], out.data_ptr())
+        hb.hp_serve_poll(server, last, -1)
+        deadline = time.perf_counter() + 120
+        while hb.hp_serve_counters(server)["completed"] < arrivals.size and time.perf_counter() < deadline:
+            time.sleep(0.01)
+        st = hb.hp_serve_stats(server)
+        c = hb.hp_serve_counters(server)
+        hb.hp_serve_destroy(server)
+        st.update({"completed": c["completed"], "steps": c["steps"], "peak_bytes": c["peak_bytes"],
+                   "peak_slots": c["peak_slots"], "max_submit_lag_ms": lag * 1e3})
+        return st
+
+    batched = serve(True)
+    plain = serve(False)
+    print(json.dumps({
+        "workload": f"Poisson {args.serve_rate:.0f} req/s for {args.serve_seconds:.0f} s, {arrivals.size} requests over "
+                    f"{n_pool} pre-generated uneven nests (FP32 compensated sums), 40 GiB budget, 4 streams",
+        "mean_iterations_per_request": iters, "offered_gbs": args.serve_rate * iters * 4 / 1e9,
+        "batched": batched, "plain_per_request": plain,
+        "p99_speedup": plain["p99_us"] / batched["p99_us"] if batched["p99_us"] else None}))
+    for n, _, _, _ in pool:
+        n.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -581,12 +647,15 @@ def main():
     ap.add_argument("--profile-b", type=int, default=0,
                     help="profiler case: run only the headline nest with this outer extent b")
     ap.add_argument("--prec", default="f32_comp", choices=["f32_comp", "f32"])
-    ap.add_argument("--workload", default="nest4", choices=["nest4", "csr", "gemv", "batch"],
+    ap.add_argument("--workload", default="nest4", choices=["nest4", "csr", "gemv", "batch", "serve"],
                     help="nest4: the headline line; csr / gemv: measurement of the other workloads")
     ap.add_argument("--csr-rows", type=int, default=1 << 22)
     ap.add_argument("--batch-nests", type=int, default=10000)
     ap.add_argument("--batch-breakdown", action="store_true", help="batch: also time each plan class alone")
     ap.add_argument("--tune", action="store_true", help="batch: autotune one nest per shape class first")
+    ap.add_argument("--serve-rate", type=float, default=20000.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-pool", type=int, default=2000)
     ap.add_argument("--no-hist", action="store_true", help="csr: SpMV without the fused histogram")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -601,6 +670,8 @@ def main():
         run_gemv_workload(args)
     elif args.workload == "batch":
         run_batch_workload(args)
+    elif args.workload == "serve":
+        run_serve_workload(args)
     else:
         run_hp(args)
 

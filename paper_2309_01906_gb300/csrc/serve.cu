@@ -337,7 +337,9 @@ void scheduler(hp_server* s) {
         }
       }
       if (st.reqs.empty()) break;
-      const hp_status h = s->batching ? launch_batched(s, st) : launch_plain(s, st);
+      // a step of one request goes straight to the single-nest kernels (same
+      // result bits, fewer API calls); larger steps run batched
+      const hp_status h = (s->batching && st.reqs.size() > 1) ? launch_batched(s, st) : launch_plain(s, st);
       if (h != HP_OK) {
         {
           std::lock_guard<std::mutex> lock(s->mu);
