@@ -504,6 +504,12 @@ def make_uneven_batch(n_nests, seed=9, tune=False, stream=None):
             "iters": int(sum(sh.size for sh in shapes))}
 
 
+def _plan_class(d):
+    """Plan class of a described nest: team / lanes or warps [/ split]."""
+    return f"{d['team']}/{d['team_lanes'] if d['team'] == 'lanes' else d['warps']}" + \
+        ("/split" if d["grid_parts"] > 1 else "")
+
+
 def run_batch_workload(args):
     """Batched uneven nests: one persistent launch per arithmetic under a CUDA graph
     vs one hp_nest_run per nest (same plans, same stream, no graph)."""
@@ -514,6 +520,18 @@ def run_batch_workload(args):
     t0 = time.perf_counter()
     wl = make_uneven_batch(args.batch_nests, tune=args.tune, stream=stream)
     setup_s = time.perf_counter() - t0
+    if args.batch_class:
+        # keep only the nests of one plan class (to time or profile it alone)
+        keep = [i for i, nest in enumerate(wl["nests"]) if _plan_class(nest.describe()) == args.batch_class]
+        if not keep:
+            raise SystemExit(f"no nest of plan class {args.batch_class!r}")
+        for i, nest in enumerate(wl["nests"]):
+            if i not in set(keep):
+                nest.close()
+        for k in ("shapes", "nests", "ins", "outs"):
+            wl[k] = [wl[k][i] for i in keep]
+        wl["bytes"] = int(sum(sh.size for sh in wl["shapes"])) * 4
+        wl["iters"] = int(sum(sh.size for sh in wl["shapes"]))
     sp = stream.cuda_stream
     handles = [n.handle for n in wl["nests"]]
     # arguments marshalled once for both forms: the timed region holds only the
@@ -534,10 +552,7 @@ def run_batch_workload(args):
         # each plan class batched alone: where the batched time goes
         classes = {}
         for idx, nest in enumerate(wl["nests"]):
-            d = nest.describe()
-            key = f"{d['team']}/{d['team_lanes'] if d['team'] == 'lanes' else d['warps']}" + \
-                ("/split" if d["grid_parts"] > 1 else "")
-            classes.setdefault(key, []).append(idx)
+            classes.setdefault(_plan_class(nest.describe()), []).append(idx)
         for key, idxs in classes.items():
             pb = hb.PreparedBatch([handles[i] for i in idxs], [wl["ins"][i] for i in idxs],
                                   [wl["outs"][i] for i in idxs])
@@ -552,8 +567,7 @@ def run_batch_workload(args):
     n = len(wl["nests"])
     teams = {}
     for nest in wl["nests"]:
-        d = nest.describe()
-        key = f"{d['team']}/{d['team_lanes'] if d['team'] == 'lanes' else d['warps']}" + ("/split" if d["grid_parts"] > 1 else "")
+        key = _plan_class(nest.describe())
         teams[key] = teams.get(key, 0) + 1
     print(json.dumps({
         "workload": f"{n} uneven nests (depth 2-5, lognormal sizes), FP32 compensated sums and int32 max",
@@ -652,6 +666,7 @@ def main():
     ap.add_argument("--csr-rows", type=int, default=1 << 22)
     ap.add_argument("--batch-nests", type=int, default=10000)
     ap.add_argument("--batch-breakdown", action="store_true", help="batch: also time each plan class alone")
+    ap.add_argument("--batch-class", default="", help="batch: keep only the nests of this plan class (e.g. lanes/1)")
     ap.add_argument("--tune", action="store_true", help="batch: autotune one nest per shape class first")
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--serve-seconds", type=float, default=60.0)

@@ -256,8 +256,10 @@ hp_status hp_nest_describe(const hp_nest *n, char *buf, size_t len);
 
 /* Wait for the stream, then read the nest's device error word (0 = none;
  * 1 = a device-side bounded wait ran out; 2 = CSR offsets or column indices
- * outside the sizes declared at create, whose entries were skipped).  Returns
- * HP_ETIMEOUT if the word is set, HP_OK otherwise. */
+ * outside the sizes declared at create, whose entries were skipped; 3 = a
+ * wait of the batched executor's shared-memory stage ring ran out of time
+ * (1 s) while a tile of this nest ran; the batch's outputs are then invalid).
+ * Returns HP_ETIMEOUT if the word is set, HP_OK otherwise. */
 hp_status hp_nest_check(hp_nest *n, void *stream, int32_t *device_error);
 
 void hp_nest_destroy(hp_nest *n);

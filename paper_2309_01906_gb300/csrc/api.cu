@@ -267,7 +267,9 @@ hp_status hp_nest_check(hp_nest* n, void* stream, int32_t* device_error) {
   if (device_error) *device_error = v;
   if (v != 0)
     return fail(HP_ETIMEOUT, "device error word set (code " + std::to_string(v) +
-                                 (v == 2 ? ": CSR offsets or columns outside the declared sizes)" : ")"));
+                                 (v == 2   ? ": CSR offsets or columns outside the declared sizes)"
+                                  : v == 3 ? ": a batched stage wait ran out of time)"
+                                           : ")"));
   return HP_OK;
 }
 

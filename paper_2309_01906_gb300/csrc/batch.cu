@@ -264,6 +264,7 @@ extern "C" hp_status hp_nest_run_batch(hp_nest* const* nests, const void* const*
     h[i].out = out_dev[i];
     h[i].part = n->part;
     h[i].tickets = ctx->ticket_off[i] >= 0 ? ctx->d_tickets + ctx->ticket_off[i] : nullptr;
+    h[i].err = n->err;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if ((e = cudaGraphLaunch(ctx->exec[b], s)) != cudaSuccess) return cuda_err(e, "batch graph launch");

@@ -1,20 +1,52 @@
 // batch_kernels.cuh — one persistent launch over the tiles of many nests.
 //
-// Every CTA takes tile after tile from an atomic counter (a dynamic schedule
-// at grid level, Sec. 3.5) until the table is exhausted.  A tile is a range of
+// Every CTA runs a dynamic schedule at grid level (Sec. 3.5): tiles are taken
+// from an atomic counter until the table is exhausted.  A tile is a range of
 // work items of one nest; it runs with that nest's own plan and with exactly
-// the per-thread fold and team tree of rect_block_kernel / rect_lanes_kernel
-// (same fold_item, same lane butterfly, same warp order), so every nest's
-// outputs equal those of hp_nest_run on it, bit for bit.  Nests split over
-// grid parts fold their parts in part order once the last part of an output
-// has arrived (a per-output ticket counter; nobody waits on it).
+// the per-thread fold order and team tree of rect_block_kernel /
+// rect_lanes_kernel, so every nest's outputs equal those of hp_nest_run on it,
+// bit for bit.  Nests split over grid parts fold their parts in part order
+// once the last part of an output has arrived (a per-output ticket counter;
+// nobody waits on it).
+//
+// The CTA is warp-specialised.  One producer warp takes the tiles, copies each
+// tile's nest descriptor into a small tile queue in shared memory and, when
+// the tile's inputs form one contiguous range (a single reduced virtual level
+// of stride 1: every planner map), streams that range through a ring of
+// shared-memory stages with 1-D bulk copies (cp.async.bulk, completion counted
+// in bytes on one mbarrier per stage).  The range is widened to 16-byte
+// granules, so any alignment of the nest's data streams at full width.  Eight
+// consumer warps fold from the ring in phases: a phase waits for the stages
+// that cover its window of iterations, folds them in the order fold_item
+// would, and releases the stages below its end.  The producer runs up to a
+// ring ahead, across item and tile boundaries, so HBM reads never drain at a
+// reduction.  Tiles that cannot stream (GEOMETRIC / AFFINE bodies, several
+// reduced virtual levels, maps without reduction) fold from global memory.
+//
+// Every wait is bounded in time: one that runs out sets the nest's device
+// error word (code 3, read by hp_nest_check) and a CTA-wide abort flag, after
+// which the CTA skips the remaining waits, leaves at the next tile boundary
+// and lets its bulk copies land before it exits.
 #pragma once
 
 #include "rect_kernels.cuh"
 
 namespace hp {
 
-constexpr int kBatchThreads = 256;   // CTA size of the persistent kernel (block teams up to 8 warps)
+constexpr int kBatchThreads = 256;                       // consumer threads: block teams of up to 8 warps
+constexpr int kBatchWarps = kBatchThreads / 32;
+constexpr int kBatchAllThreads = kBatchThreads + 32;     // + the producer warp
+constexpr int kStageBytes = 8192;                        // one ring stage
+constexpr int kStages = 8;
+constexpr int kRingBytes = kStages * kStageBytes;        // a power of two (ring offsets are masked)
+constexpr int kTileQueue = 4;                            // tiles the producer may run ahead
+constexpr int kLanesWindowBytes = kRingBytes / 2 - 16;   // largest window of a lanes-team phase
+constexpr int kBlockPhaseBytes = 2 * kStageBytes;        // window of a block-team phase (whole steps)
+constexpr unsigned long long kBatchWaitNs = 1000000000ull;  // a wait gives up after 1 s
+constexpr int32_t kErrStageWait = 3;                     // device error code of a wait that gave up
+#ifndef HP_BATCH_MIN_BLOCKS
+#define HP_BATCH_MIN_BLOCKS 3                            // resident CTAs per SM the registers are sized for
+#endif
 
 // one nest of a batch, as the device sees it
 struct BatchNest {
@@ -24,6 +56,7 @@ struct BatchNest {
   void* out;
   void* part;          // grid-part partials (G > 1)
   int32_t* tickets;    // per output (G > 1)
+  int32_t* err;        // the nest's device error word
 };
 
 struct BatchTile {
@@ -31,6 +64,46 @@ struct BatchTile {
   int32_t count;       // items
   int64_t item0;
 };
+
+// a tile as the producer hands it to the consumers
+struct BatchQueued {
+  BatchNest bn;
+  BatchTile t;
+  int64_t k0;          // ring stage (running count) holding the first byte of the stream
+  uint64_t a0;         // stream start: the tile's first input byte rounded down to 16 bytes
+  uint64_t gA;         // address of the nest's input A
+  int32_t nst;         // stages of the stream (0: the tile folds from global memory)
+  int32_t end;         // 1: no more tiles
+};
+
+// Can a nest's tiles stream through the ring?  One reduced virtual level of
+// stride 1 makes every item (and every tile: consecutive items are adjacent)
+// one contiguous range of A; a lanes-team phase must hold at least one item.
+__host__ __device__ inline bool batch_streams(const RectPlan& p) {
+  if (p.team == TEAM_MAP || p.nv != 1 || p.vstride[0] != 1 || p.R < 1) return false;
+  if (p.body != HP_BODY_LOAD && p.body != HP_BODY_DOT_BCAST) return false;
+  if (p.team == TEAM_LANES && p.R * 4 > kLanesWindowBytes) return false;
+  return true;
+}
+
+// iterations [base + lo, base + hi) of A that work item `item` folds (one reduced level)
+__host__ __device__ inline void batch_item_span(const RectPlan& p, int64_t item, int64_t& base, int64_t& lo,
+                                                int64_t& hi) {
+  if (p.G == 1) {
+    base = item * p.R;
+    lo = 0;
+    hi = p.vn[0];
+    return;
+  }
+  const int64_t o = item / p.G, g = item - o * p.G;
+  base = o * p.R;
+  lo = 0;
+  hi = p.vn[0];
+  if (p.split) {
+    lo = g * p.tile;
+    hi = (lo + p.tile < p.vn[0]) ? lo + p.tile : p.vn[0];
+  }
+}
 
 template <class Op>
 __device__ __forceinline__ void batch_emit(const RectPlan& p, const BatchNest& bn, int64_t item, typename Op::Acc a) {
@@ -65,8 +138,155 @@ __device__ __forceinline__ void batch_emit(const RectPlan& p, const BatchNest& b
   }
 }
 
+// ---------------------------------------------------------------- mbarrier / bulk-copy primitives
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile(
+      "{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile(
+      "{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar), "r"(bytes)
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+// wait until the phase of parity `parity` has completed; false when the CTA
+// aborted (if `abortable`) or the wait ran out of time
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int& abort,
+                                          bool abortable = true) {
+  if (mbar_test(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_test(bar, parity)) return true;
+    if ((i & 31u) == 0) {
+      if (abortable && abort) return false;
+      if (global_ns() - t0 > kBatchWaitNs) return false;
+    }
+  }
+}
+// 1-D bulk copy global -> shared, completion counted on `bar` in bytes
+// (both addresses 16-byte aligned, bytes a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, uint64_t src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+// barrier of the consumer warps only (the producer warp never joins it)
+__device__ __forceinline__ void consumer_sync() {
+  asm volatile("bar.sync 1, %0;\n" ::"n"(kBatchThreads) : "memory");
+}
+// the same barrier, returning to every consumer thread the OR of `flag` over
+// all of them (one decision even when the producer changes a flag meanwhile)
+__device__ __forceinline__ bool consumer_sync_or(int flag) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred pa, pr;\n setp.ne.s32 pa, %1, 0;\n bar.red.or.pred pr, 1, %2, pa;\n"
+      " selp.u32 %0, 1, 0, pr;\n}\n"
+      : "=r"(r)
+      : "r"(flag), "n"(kBatchThreads)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void lds4(uint32_t a, float (&r)[4]) {
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+               : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3])
+               : "r"(a)
+               : "memory");
+}
+__device__ __forceinline__ void lds4(uint32_t a, int32_t (&r)[4]) {
+  asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a)
+               : "memory");
+}
+__device__ __forceinline__ void lds1(uint32_t a, float& r) {
+  asm volatile("ld.shared.f32 %0, [%1];\n" : "=f"(r) : "r"(a) : "memory");
+}
+__device__ __forceinline__ void lds1(uint32_t a, int32_t& r) {
+  asm volatile("ld.shared.s32 %0, [%1];\n" : "=r"(r) : "r"(a) : "memory");
+}
+
+// ---------------------------------------------------------------- bodies reading the ring
+// Iteration e of A sits at ring byte (4 e + shift) mod kRingBytes; the
+// broadcast operand of DOT_BCAST still comes from global memory (L1/L2-resident).
+template <class Op, bool DOT>
+struct BodyRing {
+  static constexpr bool kPipeable = true;
+  static constexpr bool kDot = DOT;
+  using In = typename Op::In;
+  uint32_t ring;      // shared address of the ring
+  uint32_t shift;     // low 32 bits suffice: the offset is taken modulo kRingBytes
+  const In* w;
+  template <int V>
+  __device__ __forceinline__ Vals<Op, V> load(int64_t flat, int64_t rflat) const {
+    Vals<Op, V> v;
+    const uint32_t a = ring + ((static_cast<uint32_t>(flat) * 4u + shift) & static_cast<uint32_t>(kRingBytes - 1));
+    if constexpr (V == 4) {
+      lds4(a, v.a);
+    } else {
+#pragma unroll
+      for (int i = 0; i < V; ++i) lds1(a + 4u * i, v.a[i]);
+    }
+    if constexpr (DOT) {
+      if constexpr (V == 4) {
+        const auto r = ld_keep4(w + rflat);
+        v.b[0] = r.x;
+        v.b[1] = r.y;
+        v.b[2] = r.z;
+        v.b[3] = r.w;
+      } else {
+#pragma unroll
+        for (int i = 0; i < V; ++i) v.b[i] = ld_keep(w + rflat + i);
+      }
+    }
+    return v;
+  }
+  template <int V>
+  __device__ __forceinline__ void apply(typename Op::Acc (&acc)[V], const Vals<Op, V>& v) const {
+    if constexpr (DOT) fold_vals_dot<Op, V>(acc, v.a, v.b);
+    else fold_vals_load<Op, V>(acc, v.a);
+  }
+};
+
+// the iterations x = x0, x0 + P, ... < x1 of one thread (one reduced level, so
+// the reduced index is x itself), four loads in flight before their folds
+template <class Op, int V, class Body>
+__device__ __forceinline__ void fold_span(const Body& body, int64_t base, int64_t x0, int64_t x1, int64_t P,
+                                          typename Op::Acc (&acc)[V]) {
+  int64_t x = x0;
+  for (; x + 3 * P < x1; x += 4 * P) {
+    const auto v0 = body.template load<V>(base + x, x);
+    const auto v1 = body.template load<V>(base + x + P, x + P);
+    const auto v2 = body.template load<V>(base + x + 2 * P, x + 2 * P);
+    const auto v3 = body.template load<V>(base + x + 3 * P, x + 3 * P);
+    body.template apply<V>(acc, v0);
+    body.template apply<V>(acc, v1);
+    body.template apply<V>(acc, v2);
+    body.template apply<V>(acc, v3);
+  }
+  for (; x < x1; x += P) body.template apply<V>(acc, body.template load<V>(base + x, x));
+}
+
+// ---------------------------------------------------------------- tiles folded from global memory
 // items [item0, item0 + count) of a block-team nest: one item at a time, the
-// plan's W warps fold, the CTA combines them in warp order
+// plan's W warps fold, the consumer warps combine them in warp order
 template <class Op, int V, class Body>
 __device__ __forceinline__ void batch_block_items(const RectPlan& p, const Body& body, const BatchNest& bn,
                                                   int64_t item0, int count, typename Op::Acc* wsh) {
@@ -86,17 +306,17 @@ __device__ __forceinline__ void batch_block_items(const RectPlan& p, const Body&
     if (active) fold_item<Op, V>(p, body, o, g, slot, acc);
     const Acc a = lanes_allreduce<Op>(fold_vec<Op, V>(acc), 32);
     if (lane == 0 && active) wsh[warp] = a;
-    __syncthreads();
+    consumer_sync();
     if (tid == 0) {
       Acc r = wsh[0];
       for (int w = 1; w < p.W; ++w) r = Op::combine(r, wsh[w]);
       batch_emit<Op>(p, bn, item, r);
     }
-    __syncthreads();
+    consumer_sync();
   }
 }
 
-// items of a lanes-team nest: every group of L lanes of the CTA is a team
+// items of a lanes-team nest: every group of L lanes of the consumer warps is a team
 template <class Op, int V, class Body>
 __device__ __forceinline__ void batch_lanes_items(const RectPlan& p, const Body& body, const BatchNest& bn,
                                                   int64_t item0, int count) {
@@ -108,7 +328,7 @@ __device__ __forceinline__ void batch_lanes_items(const RectPlan& p, const Body&
   int32_t slot[kMaxV];
 #pragma unroll
   for (int v = 0; v < kMaxV; ++v) slot[v] = grp * p.cg[v] + lig * p.cl[v];
-  const int teams = (blockDim.x >> 5) * (32 / L);
+  const int teams = kBatchWarps * (32 / L);
   const int team = tid / L;
   for (int b = 0; b < count; b += teams) {
     const bool valid = b + team < count;
@@ -128,13 +348,139 @@ __device__ __forceinline__ void batch_lanes_items(const RectPlan& p, const Body&
 // a nest without reduction: one output per iteration
 template <class Op, class Body>
 __device__ __forceinline__ void batch_map_items(const Body& body, const BatchNest& bn, int64_t item0, int count) {
-  for (int k = threadIdx.x; k < count; k += blockDim.x) {
+  for (int k = threadIdx.x; k < count; k += kBatchThreads) {
     typename Op::Acc acc[1] = {Op::ident()};
     body.template fold<1>(acc, item0 + k, 0);
     static_cast<typename Op::Out*>(bn.out)[item0 + k] = Op::finish(acc[0]);
   }
 }
 
+// ---------------------------------------------------------------- tiles streamed through the ring
+// Consumer-side view of the ring for one tile.  `ready` (stages this thread
+// has seen complete) and `rel` (stages this warp has released) run over the
+// CTA's whole stage sequence and advance identically in every thread.
+struct RingView {
+  uint32_t full, empty;   // shared addresses of the stage barriers
+  int64_t k0;             // first stage of the tile
+  int64_t nst;
+  uint64_t off0;          // stream byte of iteration e is 4 e + off0 (mod 2^64; off0 = A - a0)
+  const volatile int* abort;
+  int32_t* err;
+};
+
+// ring stage index holding iteration e of the tile's nest
+__device__ __forceinline__ int64_t ring_stage(const RingView& r, int64_t e) {
+  return r.k0 + static_cast<int64_t>((static_cast<uint64_t>(e) * 4u + r.off0) / kStageBytes);
+}
+// wait until every stage holding iterations [e_lo, e_hi) has landed
+__device__ __forceinline__ void ring_wait(const RingView& r, int64_t e_hi, int64_t& ready) {
+  const int64_t last = ring_stage(r, e_hi - 1);
+  for (; ready <= last; ++ready) {
+    const uint32_t bar = r.full + 8u * static_cast<uint32_t>(ready % kStages);
+    if (!mbar_wait(bar, static_cast<uint32_t>((ready / kStages) & 1), *r.abort)) {
+      if (!*r.abort) {
+        *const_cast<volatile int*>(r.abort) = 1;
+        if (r.err) atomicExch(r.err, kErrStageWait);
+      }
+    }
+  }
+}
+// release (for this warp) every stage below the one holding iteration e_end
+__device__ __forceinline__ void ring_release(const RingView& r, int64_t lim, int64_t& rel) {
+  if (rel >= lim) return;
+  __syncwarp();   // every lane's reads of these stages are done
+  for (; rel < lim; ++rel)
+    if ((threadIdx.x & 31) == 0) mbar_arrive(r.empty + 8u * static_cast<uint32_t>(rel % kStages));
+}
+
+// block team, streamed.  Items go in chunks of up to kMaxM: each item is
+// folded in phases of whole steps (about two stages; a short remainder joins
+// the last phase), its warp partials are parked in shared memory, and after
+// one consumer barrier per chunk the first threads combine and emit the
+// chunk's items in parallel (the ticket round trips of split items overlap).
+// The partials alternate between two buffers, so nobody waits for the emits.
+template <class Op, int V, class Body>
+__device__ __forceinline__ void ring_block_items(const RectPlan& p, const Body& body, const BatchNest& bn,
+                                                 int64_t item0, int count, const RingView& rv, int64_t& ready,
+                                                 int64_t& rel, typename Op::Acc (*wsh)[kMaxM][kBatchWarps]) {
+  using Acc = typename Op::Acc;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool active = warp < p.W;
+  const int grp = lane / p.grp_lanes, lig = lane % p.grp_lanes;
+  const int64_t s0 = warp * p.cw[0] + grp * p.cg[0] + lig * p.cl[0];
+  const int64_t P = p.vP[0];
+  const int64_t KP = P * ((kBlockPhaseBytes / 4) / P > 0 ? (kBlockPhaseBytes / 4) / P : 1);
+  int buf = 0;
+  for (int m0 = 0; m0 < count; m0 += kMaxM, buf ^= 1) {
+    const int mc = (count - m0 < kMaxM) ? count - m0 : kMaxM;
+    for (int m = 0; m < mc; ++m) {
+      int64_t base, lo, hi;
+      batch_item_span(p, item0 + m0 + m, base, lo, hi);
+      Acc acc[V];
+#pragma unroll
+      for (int i = 0; i < V; ++i) acc[i] = Op::ident();
+      for (int64_t w0 = lo; w0 < hi;) {
+        int64_t w1 = (w0 + KP < hi) ? w0 + KP : hi;
+        if (hi - w1 < KP / 2) w1 = hi;
+        ring_wait(rv, base + w1, ready);
+        if (active) fold_span<Op, V>(body, base, w0 + s0, w1, P, acc);
+        ring_release(rv, ring_stage(rv, base + w1), rel);
+        w0 = w1;
+      }
+      const Acc a = lanes_allreduce<Op>(fold_vec<Op, V>(acc), 32);
+      if (lane == 0 && active) wsh[buf][m][warp] = a;
+    }
+    consumer_sync();
+    if (tid < mc) {
+      Acc r = wsh[buf][tid][0];
+      for (int w = 1; w < p.W; ++w) r = Op::combine(r, wsh[buf][tid][w]);
+      batch_emit<Op>(p, bn, item0 + m0 + tid, r);
+    }
+  }
+}
+
+// lanes teams, streamed: a phase holds as many consecutive items as fit half
+// the ring, in whole rounds of one item per team where possible; each team
+// folds the items of its index in every round
+template <class Op, int V, class Body>
+__device__ __forceinline__ void ring_lanes_items(const RectPlan& p, const Body& body, const BatchNest& bn,
+                                                 int64_t item0, int count, const RingView& rv, int64_t& ready,
+                                                 int64_t& rel) {
+  using Acc = typename Op::Acc;
+  const int L = p.L;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int lt = lane % L;
+  const int grp = lt / p.grp_lanes, lig = lt % p.grp_lanes;
+  const int64_t s0 = grp * p.cg[0] + lig * p.cl[0];
+  const int64_t P = p.vP[0];
+  const int teams = kBatchWarps * (32 / L);
+  const int team = tid / L;
+  const int64_t fit = kLanesWindowBytes / (4 * p.R);
+  const int per = static_cast<int>(fit >= teams ? (fit / teams) * teams : (fit > 0 ? fit : 1));
+  for (int b = 0; b < count; b += per) {
+    const int n = (count - b < per) ? count - b : per;
+    int64_t base, lo, hi;
+    batch_item_span(p, item0 + b + n - 1, base, lo, hi);
+    const int64_t w_end = base + hi;
+    ring_wait(rv, w_end, ready);
+    for (int j0 = 0; j0 < n; j0 += teams) {   // the same trip count in every lane
+      const int j = j0 + team;
+      const bool valid = j < n;
+      Acc acc[V];
+#pragma unroll
+      for (int i = 0; i < V; ++i) acc[i] = Op::ident();
+      if (valid) {
+        batch_item_span(p, item0 + b + j, base, lo, hi);
+        fold_span<Op, V>(body, base, lo + s0, hi, P, acc);
+      }
+      const Acc a = lanes_allreduce<Op>(fold_vec<Op, V>(acc), L);
+      if (valid && lt == 0) batch_emit<Op>(p, bn, item0 + b + j, a);
+    }
+    ring_release(rv, ring_stage(rv, w_end), rel);
+  }
+}
+
+// ---------------------------------------------------------------- one tile, consumer side
 template <class Op, class Body>
 __device__ __forceinline__ void batch_tile(const RectPlan& p, const Body& body, const BatchNest& bn, const BatchTile& t,
                                            typename Op::Acc* wsh) {
@@ -149,48 +495,173 @@ __device__ __forceinline__ void batch_tile(const RectPlan& p, const Body& body, 
   }
 }
 
+template <class Op, bool DOT>
+__device__ __forceinline__ void ring_tile(const BatchQueued& e, uint32_t ring, const RingView& rv, int64_t& ready,
+                                          int64_t& rel, typename Op::Acc (*wsh)[kMaxM][kBatchWarps]) {
+  const RectPlan& p = e.bn.rp;
+  BodyRing<Op, DOT> body;
+  body.ring = ring;
+  body.shift = static_cast<uint32_t>(rv.off0 + static_cast<uint64_t>(rv.k0 % kStages) * kStageBytes);
+  body.w = static_cast<const typename Op::In*>(e.bn.in1);
+  if (p.team == TEAM_BLOCK) {
+    if (p.V == 4) ring_block_items<Op, 4>(p, body, e.bn, e.t.item0, e.t.count, rv, ready, rel, wsh);
+    else ring_block_items<Op, 1>(p, body, e.bn, e.t.item0, e.t.count, rv, ready, rel, wsh);
+  } else {
+    if (p.V == 4) ring_lanes_items<Op, 4>(p, body, e.bn, e.t.item0, e.t.count, rv, ready, rel);
+    else ring_lanes_items<Op, 1>(p, body, e.bn, e.t.item0, e.t.count, rv, ready, rel);
+  }
+}
+
+// ---------------------------------------------------------------- producer warp
+__device__ __forceinline__ void batch_producer(const BatchNest* __restrict__ nests,
+                                               const BatchTile* __restrict__ tiles, int64_t n_tiles,
+                                               unsigned long long* counter, BatchQueued* tq, uint32_t ring,
+                                               uint32_t full, uint32_t empty, uint32_t tq_full, uint32_t tq_empty,
+                                               volatile int& abort) {
+  const int lane = threadIdx.x & 31;
+  int64_t kst = 0;   // stages issued so far
+  for (int64_t q = 0;; ++q) {
+    const int s = static_cast<int>(q % kTileQueue);
+    int ok = 1;
+    if (lane == 0) ok = mbar_wait(tq_empty + 8u * s, static_cast<uint32_t>(((q / kTileQueue) & 1) ^ 1), abort);
+    if (!__shfl_sync(~0u, ok, 0)) break;   // consumers gave up: they leave at their next tile boundary
+    unsigned long long k = 0;
+    if (lane == 0) k = atomicAdd(counter, 1ull);
+    k = __shfl_sync(~0u, k, 0);
+    BatchQueued& e = tq[s];
+    if (static_cast<int64_t>(k) >= n_tiles) {
+      if (lane == 0) e.end = 1;
+      mbar_arrive(tq_full + 8u * s);
+      break;
+    }
+    const BatchTile t = tiles[k];
+    {
+      const int32_t* src = reinterpret_cast<const int32_t*>(nests + t.nest);
+      int32_t* dst = reinterpret_cast<int32_t*>(&e.bn);
+      for (int i = lane; i < static_cast<int>(sizeof(BatchNest) / 4); i += 32) dst[i] = src[i];
+    }
+    __syncwarp();
+    const RectPlan& p = e.bn.rp;
+    int64_t nst = 0;
+    uint64_t a0 = 0, a1 = 0, gA = 0;
+    if (batch_streams(p) && e.bn.in0 != nullptr && t.count > 0) {
+      int64_t b0, l0, h0, b1, l1, h1;
+      batch_item_span(p, t.item0, b0, l0, h0);
+      batch_item_span(p, t.item0 + t.count - 1, b1, l1, h1);
+      gA = reinterpret_cast<uint64_t>(e.bn.in0);
+      a0 = (gA + 4u * static_cast<uint64_t>(b0 + l0)) & ~uint64_t(15);
+      a1 = (gA + 4u * static_cast<uint64_t>(b1 + h1) + 15u) & ~uint64_t(15);
+      if (a1 > a0) nst = static_cast<int64_t>((a1 - a0 + kStageBytes - 1) / kStageBytes);
+    }
+    if (lane == 0) {
+      e.t = t;
+      e.k0 = kst;
+      e.a0 = a0;
+      e.gA = gA;
+      e.nst = static_cast<int32_t>(nst);
+      e.end = 0;
+    }
+    __syncwarp();
+    mbar_arrive(tq_full + 8u * s);   // every lane releases the words it wrote
+    if (lane == 0) {
+      for (int64_t i = 0; i < nst; ++i) {
+        const int64_t kk = kst + i;
+        const uint32_t slot = static_cast<uint32_t>(kk % kStages);
+        if (!mbar_wait(empty + 8u * slot, static_cast<uint32_t>(((kk / kStages) & 1) ^ 1), abort)) {
+          if (!abort) {
+            abort = 1;
+            if (e.bn.err) atomicExch(e.bn.err, kErrStageWait);
+          }
+          nst = i;   // stages not issued are never waited for (the CTA is aborting)
+          break;
+        }
+        const uint64_t src = a0 + static_cast<uint64_t>(i) * kStageBytes;
+        const uint32_t bytes = static_cast<uint32_t>(a1 - src < kStageBytes ? a1 - src : kStageBytes);
+        mbar_arrive_tx(full + 8u * slot, bytes);
+        bulk_g2s(ring + slot * kStageBytes, src, bytes, full + 8u * slot);
+      }
+    }
+    kst += __shfl_sync(~0u, nst, 0);
+    if (abort) break;
+  }
+  // let the copies in flight land before the warp exits (the last ring of stages)
+  if (lane == 0)
+    for (int64_t kk = kst > kStages ? kst - kStages : 0; kk < kst; ++kk)
+      mbar_wait(full + 8u * static_cast<uint32_t>(kk % kStages), static_cast<uint32_t>((kk / kStages) & 1), abort,
+                false);
+}
+
+// ---------------------------------------------------------------- the persistent kernel
 template <class Op>
-__global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchNest* __restrict__ nests,
-                                                              const BatchTile* __restrict__ tiles, int64_t n_tiles,
-                                                              unsigned long long* counter) {
+__global__ void __launch_bounds__(kBatchAllThreads, HP_BATCH_MIN_BLOCKS)
+    batch_kernel(const BatchNest* __restrict__ nests, const BatchTile* __restrict__ tiles, int64_t n_tiles,
+                 unsigned long long* counter) {
   using Acc = typename Op::Acc;
   using In = typename Op::In;
-  __shared__ BatchNest sn;
-  __shared__ BatchTile st;
-  __shared__ long long next;
-  __shared__ Acc wsh[kBatchThreads / 32];
-  while (true) {
-    if (threadIdx.x == 0) next = static_cast<long long>(atomicAdd(counter, 1ull));
-    __syncthreads();
-    const long long k = next;
-    if (k >= n_tiles) break;
-    if (threadIdx.x == 0) {
-      st = tiles[k];
-      sn = nests[st.nest];
+  extern __shared__ __align__(128) unsigned char batch_ring[];
+  __shared__ __align__(8) unsigned long long bars[2 * kStages + 2 * kTileQueue];
+  __shared__ BatchQueued tq[kTileQueue];
+  __shared__ Acc wsh[2][kMaxM][kBatchWarps];
+  __shared__ int abort_flag;
+  const uint32_t ring = smem_u32(batch_ring);
+  const uint32_t full = smem_u32(&bars[0]), empty = full + 8u * kStages;
+  const uint32_t tq_full = empty + 8u * kStages, tq_empty = tq_full + 8u * kTileQueue;
+  volatile int& abort = abort_flag;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(full + 8u * i, 1);
+      mbar_init(empty + 8u * i, kBatchWarps);
     }
-    __syncthreads();
-    const RectPlan& p = sn.rp;
-    switch (p.body) {
-      case HP_BODY_LOAD: {
-        BodyLoad<Op> b{static_cast<const In*>(sn.in0)};
-        batch_tile<Op>(p, b, sn, st, wsh);
-        break;
-      }
-      case HP_BODY_DOT_BCAST: {
-        BodyDot<Op> b{static_cast<const In*>(sn.in0), static_cast<const In*>(sn.in1)};
-        batch_tile<Op>(p, b, sn, st, wsh);
-        break;
-      }
-      default: {
-        BodyAffine<Op> b;
-        b.a = p.aff_a;
-        b.b = p.aff_b;
-        b.m = p.aff_m;
-        batch_tile<Op>(p, b, sn, st, wsh);
-        break;
+    for (int i = 0; i < kTileQueue; ++i) {
+      mbar_init(tq_full + 8u * i, 32);
+      mbar_init(tq_empty + 8u * i, kBatchThreads);
+    }
+    abort = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x >= kBatchThreads) {
+    batch_producer(nests, tiles, n_tiles, counter, tq, ring, full, empty, tq_full, tq_empty, abort);
+    return;
+  }
+  int64_t ready = 0, rel = 0;
+  for (int64_t q = 0;; ++q) {
+    const int s = static_cast<int>(q % kTileQueue);
+    if (!mbar_wait(tq_full + 8u * s, static_cast<uint32_t>((q / kTileQueue) & 1), abort) && !abort) {
+      abort = 1;
+      if (nests[0].err) atomicExch(nests[0].err, kErrStageWait);
+    }
+    if (consumer_sync_or(abort)) break;   // one decision for all consumer warps
+    const BatchQueued& e = tq[s];
+    if (e.end) break;
+    const RectPlan& p = e.bn.rp;
+    if (e.nst > 0) {
+      RingView rv{full, empty, e.k0, e.nst, e.gA - e.a0, &abort_flag, e.bn.err};
+      if (p.body == HP_BODY_DOT_BCAST) ring_tile<Op, true>(e, ring, rv, ready, rel, wsh);
+      else ring_tile<Op, false>(e, ring, rv, ready, rel, wsh);
+      ring_release(rv, e.k0 + e.nst, rel);
+    } else {
+      switch (p.body) {
+        case HP_BODY_LOAD: {
+          BodyLoad<Op> b{static_cast<const In*>(e.bn.in0)};
+          batch_tile<Op>(p, b, e.bn, e.t, &wsh[0][0][0]);
+          break;
+        }
+        case HP_BODY_DOT_BCAST: {
+          BodyDot<Op> b{static_cast<const In*>(e.bn.in0), static_cast<const In*>(e.bn.in1)};
+          batch_tile<Op>(p, b, e.bn, e.t, &wsh[0][0][0]);
+          break;
+        }
+        default: {
+          BodyAffine<Op> b;
+          b.a = p.aff_a;
+          b.b = p.aff_b;
+          b.m = p.aff_m;
+          batch_tile<Op>(p, b, e.bn, e.t, &wsh[0][0][0]);
+          break;
+        }
       }
     }
-    __syncthreads();  // the tile's shared state is rewritten next
+    mbar_arrive(tq_empty + 8u * s);   // this thread is done with the entry
   }
 }
 
@@ -204,15 +675,25 @@ struct BatchLaunch {
 };
 
 template <class Op>
+inline cudaError_t batch_prepare() {
+  static const cudaError_t e =
+      cudaFuncSetAttribute(batch_kernel<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRingBytes);
+  return e;
+}
+
+template <class Op>
 inline cudaError_t launch_batch_op(const BatchLaunch& b, cudaStream_t st) {
-  batch_kernel<Op><<<b.grid, kBatchThreads, 0, st>>>(b.nests, b.tiles, b.n_tiles, b.counter);
+  cudaError_t e = batch_prepare<Op>();
+  if (e != cudaSuccess) return e;
+  batch_kernel<Op><<<b.grid, kBatchAllThreads, kRingBytes, st>>>(b.nests, b.tiles, b.n_tiles, b.counter);
   return cudaPeekAtLastError();
 }
 
 template <class Op>
 inline int batch_blocks_per_sm() {
+  if (batch_prepare<Op>() != cudaSuccess) return 1;
   int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<Op>, kBatchThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<Op>, kBatchAllThreads, kRingBytes);
   return n < 1 ? 1 : n;
 }
 

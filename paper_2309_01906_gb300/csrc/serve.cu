@@ -234,6 +234,7 @@ hp_status launch_batched(hp_server* s, Step& st) {
     bn.part = r.part_bytes ? static_cast<char*>(s->part_pool) + r.part_off : nullptr;
     bn.tickets = r.ticket_bytes ? reinterpret_cast<int32_t*>(reinterpret_cast<char*>(s->ticket_pool) + r.ticket_off)
                                 : nullptr;
+    bn.err = r.nest->err;
     step_tiles(static_cast<int>(i), p.rp, target, tiles[batch_combo(p.prec, p.op)]);
   }
   size_t n_tiles = 0;
