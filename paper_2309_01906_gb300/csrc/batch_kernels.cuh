@@ -105,37 +105,49 @@ __host__ __device__ inline void batch_item_span(const RectPlan& p, int64_t item,
   }
 }
 
+// where a nest's results go (copied to registers for the streamed paths)
+struct EmitTo {
+  void* out;
+  void* part;          // grid-part partials (G > 1)
+  int32_t* tickets;    // per output (G > 1)
+  int32_t G;
+};
+
 template <class Op>
-__device__ __forceinline__ void batch_emit(const RectPlan& p, const BatchNest& bn, int64_t item, typename Op::Acc a) {
+__device__ __forceinline__ void batch_emit(const EmitTo& to, int64_t item, typename Op::Acc a) {
   using Acc = typename Op::Acc;
-  if (p.G == 1) {
-    static_cast<typename Op::Out*>(bn.out)[item] = Op::finish(a);
+  if (to.G == 1) {
+    static_cast<typename Op::Out*>(to.out)[item] = Op::finish(a);
     return;
   }
-  Acc* part = static_cast<Acc*>(bn.part);
-  const int64_t o = item / p.G;
+  Acc* part = static_cast<Acc*>(to.part);
+  const int64_t o = item / to.G;
   part[item] = a;
   __threadfence();  // publish the partial before taking the ticket
-  if (atomicAdd(&bn.tickets[o], 1) == p.G - 1) {
+  if (atomicAdd(&to.tickets[o], 1) == to.G - 1) {
     __threadfence();  // all parts of this output are visible
-    const Acc* pp = part + o * p.G;
+    const Acc* pp = part + o * to.G;
     if constexpr (sizeof(Acc) == 8 && Op::kFp) {
       // compensated partials: the final grid-level combine in FP64, part order
       const volatile float* pv = reinterpret_cast<const volatile float*>(pp);
       double s = 0.0;
-      for (int g = 0; g < p.G; ++g) {
+      for (int g = 0; g < to.G; ++g) {
         s += static_cast<double>(pv[2 * g]);
         s += static_cast<double>(pv[2 * g + 1]);
       }
-      static_cast<typename Op::Out*>(bn.out)[o] = static_cast<float>(s);
+      static_cast<typename Op::Out*>(to.out)[o] = static_cast<float>(s);
     } else {
       const volatile Acc* pv = pp;
       Acc v = pv[0];
-      for (int g = 1; g < p.G; ++g) v = Op::combine(v, pv[g]);
-      static_cast<typename Op::Out*>(bn.out)[o] = Op::finish(v);
+      for (int g = 1; g < to.G; ++g) v = Op::combine(v, pv[g]);
+      static_cast<typename Op::Out*>(to.out)[o] = Op::finish(v);
     }
-    bn.tickets[o] = 0;  // ready for the next run
+    to.tickets[o] = 0;  // ready for the next run
   }
+}
+template <class Op>
+__device__ __forceinline__ void batch_emit(const RectPlan& p, const BatchNest& bn, int64_t item, typename Op::Acc a) {
+  batch_emit<Op>(EmitTo{bn.out, bn.part, bn.tickets, p.G}, item, a);
 }
 
 // ---------------------------------------------------------------- mbarrier / bulk-copy primitives
@@ -166,19 +178,29 @@ __device__ __forceinline__ unsigned long long global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
   return t;
 }
-// wait until the phase of parity `parity` has completed; false when the CTA
-// aborted (if `abortable`) or the wait ran out of time
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int& abort,
-                                          bool abortable = true) {
-  if (mbar_test(bar, parity)) return true;
+__device__ __forceinline__ int ld_abort(uint32_t at) {
+  int v;
+  asm volatile("ld.volatile.shared.s32 %0, [%1];\n" : "=r"(v) : "r"(at) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_abort(uint32_t at) {
+  asm volatile("st.volatile.shared.s32 [%0], 1;\n" ::"r"(at) : "memory");
+}
+// the slow part of a wait: poll until the phase of parity `parity` completes;
+// false when the CTA's abort flag (shared address abort_at, 0 = none) is set
+// or the wait ran out of time
+static __device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, uint32_t abort_at) {
   const unsigned long long t0 = global_ns();
   for (uint32_t i = 1;; ++i) {
     if (mbar_test(bar, parity)) return true;
     if ((i & 31u) == 0) {
-      if (abortable && abort) return false;
+      if (abort_at && ld_abort(abort_at)) return false;
       if (global_ns() - t0 > kBatchWaitNs) return false;
     }
   }
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t abort_at) {
+  return mbar_test(bar, parity) || mbar_wait_slow(bar, parity, abort_at);
 }
 // 1-D bulk copy global -> shared, completion counted on `bar` in bytes
 // (both addresses 16-byte aligned, bytes a multiple of 16)
@@ -207,37 +229,34 @@ __device__ __forceinline__ bool consumer_sync_or(int flag) {
 __device__ __forceinline__ void lds4(uint32_t a, float (&r)[4]) {
   asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n"
                : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3])
-               : "r"(a)
-               : "memory");
+               : "r"(a));
 }
 __device__ __forceinline__ void lds4(uint32_t a, int32_t (&r)[4]) {
   asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];\n"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(a)
-               : "memory");
+               : "r"(a));
 }
 __device__ __forceinline__ void lds1(uint32_t a, float& r) {
-  asm volatile("ld.shared.f32 %0, [%1];\n" : "=f"(r) : "r"(a) : "memory");
+  asm volatile("ld.shared.f32 %0, [%1];\n" : "=f"(r) : "r"(a));
 }
 __device__ __forceinline__ void lds1(uint32_t a, int32_t& r) {
-  asm volatile("ld.shared.s32 %0, [%1];\n" : "=r"(r) : "r"(a) : "memory");
+  asm volatile("ld.shared.s32 %0, [%1];\n" : "=r"(r) : "r"(a));
 }
 
-// ---------------------------------------------------------------- bodies reading the ring
-// Iteration e of A sits at ring byte (4 e + shift) mod kRingBytes; the
-// broadcast operand of DOT_BCAST still comes from global memory (L1/L2-resident).
+// ---------------------------------------------------------------- folding from the ring
+// Iteration e of A sits at ring byte (4 e + shift) mod kRingBytes (32-bit
+// arithmetic suffices: only the low bits survive the mask); the broadcast
+// operand of DOT_BCAST still comes from global memory (L1/L2-resident).
 template <class Op, bool DOT>
-struct BodyRing {
-  static constexpr bool kPipeable = true;
-  static constexpr bool kDot = DOT;
+struct RingFold {
   using In = typename Op::In;
   uint32_t ring;      // shared address of the ring
-  uint32_t shift;     // low 32 bits suffice: the offset is taken modulo kRingBytes
+  uint32_t shift;
   const In* w;
   template <int V>
-  __device__ __forceinline__ Vals<Op, V> load(int64_t flat, int64_t rflat) const {
+  __device__ __forceinline__ Vals<Op, V> load(uint32_t off, const In* wp, int32_t x) const {
     Vals<Op, V> v;
-    const uint32_t a = ring + ((static_cast<uint32_t>(flat) * 4u + shift) & static_cast<uint32_t>(kRingBytes - 1));
+    const uint32_t a = ring + ((off + 4u * static_cast<uint32_t>(x)) & static_cast<uint32_t>(kRingBytes - 1));
     if constexpr (V == 4) {
       lds4(a, v.a);
     } else {
@@ -246,14 +265,14 @@ struct BodyRing {
     }
     if constexpr (DOT) {
       if constexpr (V == 4) {
-        const auto r = ld_keep4(w + rflat);
+        const auto r = ld_keep4(wp + x);
         v.b[0] = r.x;
         v.b[1] = r.y;
         v.b[2] = r.z;
         v.b[3] = r.w;
       } else {
 #pragma unroll
-        for (int i = 0; i < V; ++i) v.b[i] = ld_keep(w + rflat + i);
+        for (int i = 0; i < V; ++i) v.b[i] = ld_keep(wp + x + i);
       }
     }
     return v;
@@ -263,25 +282,57 @@ struct BodyRing {
     if constexpr (DOT) fold_vals_dot<Op, V>(acc, v.a, v.b);
     else fold_vals_load<Op, V>(acc, v.a);
   }
+  // the thread's iterations lo + x for x = x0, x0 + P, ... < x1 of the item
+  // whose reduced level starts at flat iteration `first` (= base + lo), in
+  // the order fold_item visits them, several loads in flight before their folds
+  template <int V>
+  __device__ __forceinline__ void run(int64_t first, int64_t lo, int32_t x0, int32_t x1, int32_t P,
+                                      typename Op::Acc (&acc)[V]) const {
+    const uint32_t off = static_cast<uint32_t>(first) * 4u + shift;
+    const In* wp = DOT ? w + lo : nullptr;
+    int32_t x = x0;
+    if constexpr (V == 1) {
+      for (; x + 3 * P < x1; x += 4 * P) {
+        const auto v0 = load<V>(off, wp, x);
+        const auto v1 = load<V>(off, wp, x + P);
+        const auto v2 = load<V>(off, wp, x + 2 * P);
+        const auto v3 = load<V>(off, wp, x + 3 * P);
+        apply<V>(acc, v0);
+        apply<V>(acc, v1);
+        apply<V>(acc, v2);
+        apply<V>(acc, v3);
+      }
+    } else {
+      for (; x + P < x1; x += 2 * P) {
+        const auto v0 = load<V>(off, wp, x);
+        const auto v1 = load<V>(off, wp, x + P);
+        apply<V>(acc, v0);
+        apply<V>(acc, v1);
+      }
+    }
+    for (; x < x1; x += P) apply<V>(acc, load<V>(off, wp, x));
+  }
 };
 
-// the iterations x = x0, x0 + P, ... < x1 of one thread (one reduced level, so
-// the reduced index is x itself), four loads in flight before their folds
-template <class Op, int V, class Body>
-__device__ __forceinline__ void fold_span(const Body& body, int64_t base, int64_t x0, int64_t x1, int64_t P,
-                                          typename Op::Acc (&acc)[V]) {
-  int64_t x = x0;
-  for (; x + 3 * P < x1; x += 4 * P) {
-    const auto v0 = body.template load<V>(base + x, x);
-    const auto v1 = body.template load<V>(base + x + P, x + P);
-    const auto v2 = body.template load<V>(base + x + 2 * P, x + 2 * P);
-    const auto v3 = body.template load<V>(base + x + 3 * P, x + 3 * P);
-    body.template apply<V>(acc, v0);
-    body.template apply<V>(acc, v1);
-    body.template apply<V>(acc, v2);
-    body.template apply<V>(acc, v3);
+// geometry of a streamed nest, in registers
+struct RingGeom {
+  int64_t R;           // reduced iterations per output
+  int64_t vn0;         // extent of the (single) reduced virtual level
+  int64_t tile;        // iterations per grid part
+  int32_t G;           // grid parts per output
+  int32_t P;           // slots of the reduced level: iterations per step
+};
+__device__ __forceinline__ void ring_span(const RingGeom& g, int64_t item, int64_t& base, int64_t& lo, int64_t& hi) {
+  if (g.G == 1) {
+    base = item * g.R;
+    lo = 0;
+    hi = g.vn0;
+    return;
   }
-  for (; x < x1; x += P) body.template apply<V>(acc, body.template load<V>(base + x, x));
+  const int64_t o = item / g.G, part = item - o * g.G;
+  base = o * g.R;
+  lo = part * g.tile;
+  hi = (lo + g.tile < g.vn0) ? lo + g.tile : g.vn0;
 }
 
 // ---------------------------------------------------------------- tiles folded from global memory
@@ -360,37 +411,39 @@ __device__ __forceinline__ void batch_map_items(const Body& body, const BatchNes
 // has seen complete) and `rel` (stages this warp has released) run over the
 // CTA's whole stage sequence and advance identically in every thread.
 struct RingView {
-  uint32_t full, empty;   // shared addresses of the stage barriers
+  uint32_t full, empty;   // shared addresses of the stage barriers; the abort flag sits 8 bytes below `full`
+  uint32_t errp;          // shared address of the tile's pointer to its nest's error word
   int64_t k0;             // first stage of the tile
-  int64_t nst;
   uint64_t off0;          // stream byte of iteration e is 4 e + off0 (mod 2^64; off0 = A - a0)
-  const volatile int* abort;
-  int32_t* err;
 };
+
+// a stage wait of tile `rv` gave up: abort the CTA, flag the nest
+static __device__ __noinline__ void ring_give_up(uint32_t full, uint32_t errp) {
+  if (ld_abort(full - 8u)) return;
+  st_abort(full - 8u);
+  unsigned long long e;
+  asm volatile("ld.shared.u64 %0, [%1];\n" : "=l"(e) : "r"(errp) : "memory");
+  if (e) atomicExch(reinterpret_cast<int32_t*>(e), kErrStageWait);
+}
 
 // ring stage index holding iteration e of the tile's nest
 __device__ __forceinline__ int64_t ring_stage(const RingView& r, int64_t e) {
   return r.k0 + static_cast<int64_t>((static_cast<uint64_t>(e) * 4u + r.off0) / kStageBytes);
 }
-// wait until every stage holding iterations [e_lo, e_hi) has landed
+// wait until every stage holding iterations before e_hi has landed
 __device__ __forceinline__ void ring_wait(const RingView& r, int64_t e_hi, int64_t& ready) {
   const int64_t last = ring_stage(r, e_hi - 1);
   for (; ready <= last; ++ready) {
-    const uint32_t bar = r.full + 8u * static_cast<uint32_t>(ready % kStages);
-    if (!mbar_wait(bar, static_cast<uint32_t>((ready / kStages) & 1), *r.abort)) {
-      if (!*r.abort) {
-        *const_cast<volatile int*>(r.abort) = 1;
-        if (r.err) atomicExch(r.err, kErrStageWait);
-      }
-    }
+    const uint32_t bar = r.full + 8u * static_cast<uint32_t>(ready & (kStages - 1));
+    if (!mbar_wait(bar, static_cast<uint32_t>((ready / kStages) & 1), r.full - 8u)) ring_give_up(r.full, r.errp);
   }
 }
-// release (for this warp) every stage below the one holding iteration e_end
+// release (for this warp) every stage below `lim`
 __device__ __forceinline__ void ring_release(const RingView& r, int64_t lim, int64_t& rel) {
   if (rel >= lim) return;
   __syncwarp();   // every lane's reads of these stages are done
   for (; rel < lim; ++rel)
-    if ((threadIdx.x & 31) == 0) mbar_arrive(r.empty + 8u * static_cast<uint32_t>(rel % kStages));
+    if ((threadIdx.x & 31) == 0) mbar_arrive(r.empty + 8u * static_cast<uint32_t>(rel & (kStages - 1)));
 }
 
 // block team, streamed.  Items go in chunks of up to kMaxM: each item is
@@ -399,32 +452,32 @@ __device__ __forceinline__ void ring_release(const RingView& r, int64_t lim, int
 // one consumer barrier per chunk the first threads combine and emit the
 // chunk's items in parallel (the ticket round trips of split items overlap).
 // The partials alternate between two buffers, so nobody waits for the emits.
-template <class Op, int V, class Body>
-__device__ __forceinline__ void ring_block_items(const RectPlan& p, const Body& body, const BatchNest& bn,
-                                                 int64_t item0, int count, const RingView& rv, int64_t& ready,
-                                                 int64_t& rel, typename Op::Acc (*wsh)[kMaxM][kBatchWarps]) {
+template <class Op, int V, class Fold>
+__device__ __forceinline__ void ring_block_items(const RingGeom& gm, const Fold& fold, const BatchNest& bn, int W,
+                                                 int32_t s0, int64_t item0, int count, const RingView& rv,
+                                                 int64_t& ready, int64_t& rel,
+                                                 typename Op::Acc (*wsh)[kMaxM][kBatchWarps]) {
   using Acc = typename Op::Acc;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool active = warp < p.W;
-  const int grp = lane / p.grp_lanes, lig = lane % p.grp_lanes;
-  const int64_t s0 = warp * p.cw[0] + grp * p.cg[0] + lig * p.cl[0];
-  const int64_t P = p.vP[0];
-  const int64_t KP = P * ((kBlockPhaseBytes / 4) / P > 0 ? (kBlockPhaseBytes / 4) / P : 1);
+  const bool active = warp < W;
+  const int32_t P = gm.P;
+  const int32_t KP = P * ((kBlockPhaseBytes / 4) / P > 0 ? (kBlockPhaseBytes / 4) / P : 1);
   int buf = 0;
   for (int m0 = 0; m0 < count; m0 += kMaxM, buf ^= 1) {
     const int mc = (count - m0 < kMaxM) ? count - m0 : kMaxM;
     for (int m = 0; m < mc; ++m) {
       int64_t base, lo, hi;
-      batch_item_span(p, item0 + m0 + m, base, lo, hi);
+      ring_span(gm, item0 + m0 + m, base, lo, hi);
       Acc acc[V];
 #pragma unroll
       for (int i = 0; i < V; ++i) acc[i] = Op::ident();
-      for (int64_t w0 = lo; w0 < hi;) {
-        int64_t w1 = (w0 + KP < hi) ? w0 + KP : hi;
-        if (hi - w1 < KP / 2) w1 = hi;
-        ring_wait(rv, base + w1, ready);
-        if (active) fold_span<Op, V>(body, base, w0 + s0, w1, P, acc);
-        ring_release(rv, ring_stage(rv, base + w1), rel);
+      const int32_t n = static_cast<int32_t>(hi - lo);   // at most a part: below 2^31 when streamed
+      for (int32_t w0 = 0; w0 < n;) {
+        int32_t w1 = (n - w0 > KP) ? w0 + KP : n;
+        if (n - w1 < KP / 2) w1 = n;
+        ring_wait(rv, base + lo + w1, ready);
+        if (active) fold.template run<V>(base + lo, lo, w0 + s0, w1, P, acc);
+        ring_release(rv, ring_stage(rv, base + lo + w1), rel);
         w0 = w1;
       }
       const Acc a = lanes_allreduce<Op>(fold_vec<Op, V>(acc), 32);
@@ -433,8 +486,8 @@ __device__ __forceinline__ void ring_block_items(const RectPlan& p, const Body& 
     consumer_sync();
     if (tid < mc) {
       Acc r = wsh[buf][tid][0];
-      for (int w = 1; w < p.W; ++w) r = Op::combine(r, wsh[buf][tid][w]);
-      batch_emit<Op>(p, bn, item0 + m0 + tid, r);
+      for (int w = 1; w < W; ++w) r = Op::combine(r, wsh[buf][tid][w]);
+      batch_emit<Op>(bn.rp, bn, item0 + m0 + tid, r);
     }
   }
 }
@@ -442,25 +495,21 @@ __device__ __forceinline__ void ring_block_items(const RectPlan& p, const Body& 
 // lanes teams, streamed: a phase holds as many consecutive items as fit half
 // the ring, in whole rounds of one item per team where possible; each team
 // folds the items of its index in every round
-template <class Op, int V, class Body>
-__device__ __forceinline__ void ring_lanes_items(const RectPlan& p, const Body& body, const BatchNest& bn,
-                                                 int64_t item0, int count, const RingView& rv, int64_t& ready,
-                                                 int64_t& rel) {
+template <class Op, int V, class Fold>
+__device__ __forceinline__ void ring_lanes_items(const RingGeom& gm, const Fold& fold, const BatchNest& bn, int L,
+                                                 int32_t s0, int64_t item0, int count, const RingView& rv,
+                                                 int64_t& ready, int64_t& rel) {
   using Acc = typename Op::Acc;
-  const int L = p.L;
-  const int tid = threadIdx.x, lane = tid & 31;
-  const int lt = lane % L;
-  const int grp = lt / p.grp_lanes, lig = lt % p.grp_lanes;
-  const int64_t s0 = grp * p.cg[0] + lig * p.cl[0];
-  const int64_t P = p.vP[0];
+  const int tid = threadIdx.x;
+  const int lt = (tid & 31) % L;
   const int teams = kBatchWarps * (32 / L);
   const int team = tid / L;
-  const int64_t fit = kLanesWindowBytes / (4 * p.R);
+  const int64_t fit = kLanesWindowBytes / (4 * gm.R);
   const int per = static_cast<int>(fit >= teams ? (fit / teams) * teams : (fit > 0 ? fit : 1));
   for (int b = 0; b < count; b += per) {
     const int n = (count - b < per) ? count - b : per;
     int64_t base, lo, hi;
-    batch_item_span(p, item0 + b + n - 1, base, lo, hi);
+    ring_span(gm, item0 + b + n - 1, base, lo, hi);
     const int64_t w_end = base + hi;
     ring_wait(rv, w_end, ready);
     for (int j0 = 0; j0 < n; j0 += teams) {   // the same trip count in every lane
@@ -470,11 +519,11 @@ __device__ __forceinline__ void ring_lanes_items(const RectPlan& p, const Body& 
 #pragma unroll
       for (int i = 0; i < V; ++i) acc[i] = Op::ident();
       if (valid) {
-        batch_item_span(p, item0 + b + j, base, lo, hi);
-        fold_span<Op, V>(body, base, lo + s0, hi, P, acc);
+        ring_span(gm, item0 + b + j, base, lo, hi);
+        fold.template run<V>(base + lo, lo, s0, static_cast<int32_t>(hi - lo), gm.P, acc);
       }
       const Acc a = lanes_allreduce<Op>(fold_vec<Op, V>(acc), L);
-      if (valid && lt == 0) batch_emit<Op>(p, bn, item0 + b + j, a);
+      if (valid && lt == 0) batch_emit<Op>(bn.rp, bn, item0 + b + j, a);
     }
     ring_release(rv, ring_stage(rv, w_end), rel);
   }
@@ -499,16 +548,26 @@ template <class Op, bool DOT>
 __device__ __forceinline__ void ring_tile(const BatchQueued& e, uint32_t ring, const RingView& rv, int64_t& ready,
                                           int64_t& rel, typename Op::Acc (*wsh)[kMaxM][kBatchWarps]) {
   const RectPlan& p = e.bn.rp;
-  BodyRing<Op, DOT> body;
-  body.ring = ring;
-  body.shift = static_cast<uint32_t>(rv.off0 + static_cast<uint64_t>(rv.k0 % kStages) * kStageBytes);
-  body.w = static_cast<const typename Op::In*>(e.bn.in1);
+  RingFold<Op, DOT> fold;
+  fold.ring = ring;
+  fold.shift = static_cast<uint32_t>(rv.off0 + static_cast<uint64_t>(rv.k0 & (kStages - 1)) * kStageBytes);
+  fold.w = static_cast<const typename Op::In*>(e.bn.in1);
+  const RingGeom gm{p.R, p.vn[0], p.tile, p.G, p.vP[0]};
+  const int64_t item0 = e.t.item0;
+  const int count = e.t.count;
+  const int lane = threadIdx.x & 31;
   if (p.team == TEAM_BLOCK) {
-    if (p.V == 4) ring_block_items<Op, 4>(p, body, e.bn, e.t.item0, e.t.count, rv, ready, rel, wsh);
-    else ring_block_items<Op, 1>(p, body, e.bn, e.t.item0, e.t.count, rv, ready, rel, wsh);
+    const int W = p.W, warp = threadIdx.x >> 5;
+    const int grp = lane / p.grp_lanes, lig = lane % p.grp_lanes;
+    const int32_t s0 = warp * p.cw[0] + grp * p.cg[0] + lig * p.cl[0];
+    if (p.V == 4) ring_block_items<Op, 4>(gm, fold, e.bn, W, s0, item0, count, rv, ready, rel, wsh);
+    else ring_block_items<Op, 1>(gm, fold, e.bn, W, s0, item0, count, rv, ready, rel, wsh);
   } else {
-    if (p.V == 4) ring_lanes_items<Op, 4>(p, body, e.bn, e.t.item0, e.t.count, rv, ready, rel);
-    else ring_lanes_items<Op, 1>(p, body, e.bn, e.t.item0, e.t.count, rv, ready, rel);
+    const int L = p.L;
+    const int lt = lane % L;
+    const int32_t s0 = (lt / p.grp_lanes) * p.cg[0] + (lt % p.grp_lanes) * p.cl[0];
+    if (p.V == 4) ring_lanes_items<Op, 4>(gm, fold, e.bn, L, s0, item0, count, rv, ready, rel);
+    else ring_lanes_items<Op, 1>(gm, fold, e.bn, L, s0, item0, count, rv, ready, rel);
   }
 }
 
@@ -517,13 +576,13 @@ __device__ __forceinline__ void batch_producer(const BatchNest* __restrict__ nes
                                                const BatchTile* __restrict__ tiles, int64_t n_tiles,
                                                unsigned long long* counter, BatchQueued* tq, uint32_t ring,
                                                uint32_t full, uint32_t empty, uint32_t tq_full, uint32_t tq_empty,
-                                               volatile int& abort) {
+                                               uint32_t abort_at) {
   const int lane = threadIdx.x & 31;
   int64_t kst = 0;   // stages issued so far
   for (int64_t q = 0;; ++q) {
     const int s = static_cast<int>(q % kTileQueue);
     int ok = 1;
-    if (lane == 0) ok = mbar_wait(tq_empty + 8u * s, static_cast<uint32_t>(((q / kTileQueue) & 1) ^ 1), abort);
+    if (lane == 0) ok = mbar_wait(tq_empty + 8u * s, static_cast<uint32_t>(((q / kTileQueue) & 1) ^ 1), abort_at);
     if (!__shfl_sync(~0u, ok, 0)) break;   // consumers gave up: they leave at their next tile boundary
     unsigned long long k = 0;
     if (lane == 0) k = atomicAdd(counter, 1ull);
@@ -567,9 +626,9 @@ __device__ __forceinline__ void batch_producer(const BatchNest* __restrict__ nes
       for (int64_t i = 0; i < nst; ++i) {
         const int64_t kk = kst + i;
         const uint32_t slot = static_cast<uint32_t>(kk % kStages);
-        if (!mbar_wait(empty + 8u * slot, static_cast<uint32_t>(((kk / kStages) & 1) ^ 1), abort)) {
-          if (!abort) {
-            abort = 1;
+        if (!mbar_wait(empty + 8u * slot, static_cast<uint32_t>(((kk / kStages) & 1) ^ 1), abort_at)) {
+          if (!ld_abort(abort_at)) {
+            st_abort(abort_at);
             if (e.bn.err) atomicExch(e.bn.err, kErrStageWait);
           }
           nst = i;   // stages not issued are never waited for (the CTA is aborting)
@@ -582,13 +641,12 @@ __device__ __forceinline__ void batch_producer(const BatchNest* __restrict__ nes
       }
     }
     kst += __shfl_sync(~0u, nst, 0);
-    if (abort) break;
+    if (ld_abort(abort_at)) break;
   }
   // let the copies in flight land before the warp exits (the last ring of stages)
   if (lane == 0)
     for (int64_t kk = kst > kStages ? kst - kStages : 0; kk < kst; ++kk)
-      mbar_wait(full + 8u * static_cast<uint32_t>(kk % kStages), static_cast<uint32_t>((kk / kStages) & 1), abort,
-                false);
+      mbar_wait(full + 8u * static_cast<uint32_t>(kk % kStages), static_cast<uint32_t>((kk / kStages) & 1), 0u);
 }
 
 // ---------------------------------------------------------------- the persistent kernel
@@ -599,14 +657,14 @@ __global__ void __launch_bounds__(kBatchAllThreads, HP_BATCH_MIN_BLOCKS)
   using Acc = typename Op::Acc;
   using In = typename Op::In;
   extern __shared__ __align__(128) unsigned char batch_ring[];
-  __shared__ __align__(8) unsigned long long bars[2 * kStages + 2 * kTileQueue];
+  // bars[0]: the CTA's abort flag; then the stage and tile-queue barriers
+  __shared__ __align__(8) unsigned long long bars[1 + 2 * kStages + 2 * kTileQueue];
   __shared__ BatchQueued tq[kTileQueue];
   __shared__ Acc wsh[2][kMaxM][kBatchWarps];
-  __shared__ int abort_flag;
   const uint32_t ring = smem_u32(batch_ring);
-  const uint32_t full = smem_u32(&bars[0]), empty = full + 8u * kStages;
+  const uint32_t abort_at = smem_u32(&bars[0]);
+  const uint32_t full = abort_at + 8u, empty = full + 8u * kStages;
   const uint32_t tq_full = empty + 8u * kStages, tq_empty = tq_full + 8u * kTileQueue;
-  volatile int& abort = abort_flag;
   if (threadIdx.x == 0) {
     for (int i = 0; i < kStages; ++i) {
       mbar_init(full + 8u * i, 1);
@@ -616,26 +674,26 @@ __global__ void __launch_bounds__(kBatchAllThreads, HP_BATCH_MIN_BLOCKS)
       mbar_init(tq_full + 8u * i, 32);
       mbar_init(tq_empty + 8u * i, kBatchThreads);
     }
-    abort = 0;
+    bars[0] = 0;
   }
   __syncthreads();
   if (threadIdx.x >= kBatchThreads) {
-    batch_producer(nests, tiles, n_tiles, counter, tq, ring, full, empty, tq_full, tq_empty, abort);
+    batch_producer(nests, tiles, n_tiles, counter, tq, ring, full, empty, tq_full, tq_empty, abort_at);
     return;
   }
   int64_t ready = 0, rel = 0;
   for (int64_t q = 0;; ++q) {
     const int s = static_cast<int>(q % kTileQueue);
-    if (!mbar_wait(tq_full + 8u * s, static_cast<uint32_t>((q / kTileQueue) & 1), abort) && !abort) {
-      abort = 1;
+    if (!mbar_wait(tq_full + 8u * s, static_cast<uint32_t>((q / kTileQueue) & 1), abort_at) && !ld_abort(abort_at)) {
+      st_abort(abort_at);
       if (nests[0].err) atomicExch(nests[0].err, kErrStageWait);
     }
-    if (consumer_sync_or(abort)) break;   // one decision for all consumer warps
+    if (consumer_sync_or(ld_abort(abort_at))) break;   // one decision for all consumer warps
     const BatchQueued& e = tq[s];
     if (e.end) break;
     const RectPlan& p = e.bn.rp;
     if (e.nst > 0) {
-      RingView rv{full, empty, e.k0, e.nst, e.gA - e.a0, &abort_flag, e.bn.err};
+      const RingView rv{full, empty, smem_u32(&e.bn.err), e.k0, e.gA - e.a0};
       if (p.body == HP_BODY_DOT_BCAST) ring_tile<Op, true>(e, ring, rv, ready, rel, wsh);
       else ring_tile<Op, false>(e, ring, rv, ready, rel, wsh);
       ring_release(rv, e.k0 + e.nst, rel);
