@@ -36,9 +36,17 @@ namespace hp {
 constexpr int kBatchThreads = 256;                       // consumer threads: block teams of up to 8 warps
 constexpr int kBatchWarps = kBatchThreads / 32;
 constexpr int kBatchAllThreads = kBatchThreads + 32;     // + the producer warp
-constexpr int kStageBytes = 8192;                        // one ring stage
-constexpr int kStages = 8;
+#ifndef HP_BATCH_STAGE_BYTES
+#define HP_BATCH_STAGE_BYTES 8192
+#endif
+#ifndef HP_BATCH_STAGES
+#define HP_BATCH_STAGES 8
+#endif
+constexpr int kStageBytes = HP_BATCH_STAGE_BYTES;        // one ring stage
+constexpr int kStages = HP_BATCH_STAGES;
 constexpr int kRingBytes = kStages * kStageBytes;        // a power of two (ring offsets are masked)
+static_assert((kStageBytes & (kStageBytes - 1)) == 0 && (kStages & (kStages - 1)) == 0 && kStageBytes >= 1024,
+              "ring stages: powers of two");
 constexpr int kTileQueue = 4;                            // tiles the producer may run ahead
 constexpr int kLanesWindowBytes = kRingBytes / 2 - 16;   // largest window of a lanes-team phase
 constexpr int kBlockPhaseBytes = 2 * kStageBytes;        // window of a block-team phase (whole steps)
@@ -288,8 +296,13 @@ struct RingFold {
   template <int V>
   __device__ __forceinline__ void run(int64_t first, int64_t lo, int32_t x0, int32_t x1, int32_t P,
                                       typename Op::Acc (&acc)[V]) const {
-    const uint32_t off = static_cast<uint32_t>(first) * 4u + shift;
-    const In* wp = DOT ? w + lo : nullptr;
+    run_at<V>(static_cast<uint32_t>(first) * 4u + shift, DOT ? w + lo : nullptr, x0, x1, P, acc);
+  }
+  // the same with the ring byte (before the mask) of iteration lo and the
+  // broadcast operand at lo given
+  template <int V>
+  __device__ __forceinline__ void run_at(uint32_t off, const In* wp, int32_t x0, int32_t x1, int32_t P,
+                                         typename Op::Acc (&acc)[V]) const {
     int32_t x = x0;
     if constexpr (V == 1) {
       for (; x + 3 * P < x1; x += 4 * P) {
@@ -446,6 +459,34 @@ __device__ __forceinline__ void ring_release(const RingView& r, int64_t lim, int
     if ((threadIdx.x & 31) == 0) mbar_arrive(r.empty + 8u * static_cast<uint32_t>(rel & (kStages - 1)));
 }
 
+// Reduce the partials of B items (part[r] = item r) over the L lanes of a
+// team in one go: recursive halving, each step handing half of the items to
+// the xor partner and combining the lower lane's partial first.  Every item
+// gets exactly the tree that lanes_allreduce builds at the team's lane 0, at
+// about one combine per item instead of log2(L).  On return part[0] of lane
+// lt holds item lt / (L / B) (B a power of two, B <= L).
+template <class Op, int B>
+__device__ __forceinline__ void lanes_reduce_many(typename Op::Acc (&part)[B], int L, int lt) {
+  using Acc = typename Op::Acc;
+  int m = L >> 1;
+#pragma unroll
+  for (int cnt = B; cnt > 1; cnt >>= 1, m >>= 1) {
+    const bool up = (lt & m) != 0;
+#pragma unroll
+    for (int i = 0; i < cnt / 2; ++i) {
+      const Acc send = up ? part[i] : part[i + cnt / 2];
+      const Acc keep = up ? part[i + cnt / 2] : part[i];
+      const Acc recv = Op::shfl_xor(send, m, L);
+      part[i] = up ? Op::combine(recv, keep) : Op::combine(keep, recv);
+    }
+  }
+  for (; m >= 1; m >>= 1) {
+    const Acc o = Op::shfl_xor(part[0], m, L);
+    part[0] = (lt & m) ? Op::combine(o, part[0]) : Op::combine(part[0], o);
+  }
+}
+constexpr int kReduceBatch = 4;   // items reduced together
+
 // block team, streamed.  Items go in chunks of up to kMaxM: each item is
 // folded in phases of whole steps (about two stages; a short remainder joins
 // the last phase), its warp partials are parked in shared memory, and after
@@ -465,23 +506,31 @@ __device__ __forceinline__ void ring_block_items(const RingGeom& gm, const Fold&
   int buf = 0;
   for (int m0 = 0; m0 < count; m0 += kMaxM, buf ^= 1) {
     const int mc = (count - m0 < kMaxM) ? count - m0 : kMaxM;
-    for (int m = 0; m < mc; ++m) {
-      int64_t base, lo, hi;
-      ring_span(gm, item0 + m0 + m, base, lo, hi);
-      Acc acc[V];
+    for (int mb = 0; mb < mc; mb += kReduceBatch) {
+      Acc part[kReduceBatch];
 #pragma unroll
-      for (int i = 0; i < V; ++i) acc[i] = Op::ident();
-      const int32_t n = static_cast<int32_t>(hi - lo);   // at most a part: below 2^31 when streamed
-      for (int32_t w0 = 0; w0 < n;) {
-        int32_t w1 = (n - w0 > KP) ? w0 + KP : n;
-        if (n - w1 < KP / 2) w1 = n;
-        ring_wait(rv, base + lo + w1, ready);
-        if (active) fold.template run<V>(base + lo, lo, w0 + s0, w1, P, acc);
-        ring_release(rv, ring_stage(rv, base + lo + w1), rel);
-        w0 = w1;
+      for (int r = 0; r < kReduceBatch; ++r) {
+        Acc acc[V];
+#pragma unroll
+        for (int i = 0; i < V; ++i) acc[i] = Op::ident();
+        if (mb + r < mc) {
+          int64_t base, lo, hi;
+          ring_span(gm, item0 + m0 + mb + r, base, lo, hi);
+          const int32_t n = static_cast<int32_t>(hi - lo);   // at most a part: below 2^31 when streamed
+          for (int32_t w0 = 0; w0 < n;) {
+            int32_t w1 = (n - w0 > KP) ? w0 + KP : n;
+            if (n - w1 < KP / 2) w1 = n;
+            ring_wait(rv, base + lo + w1, ready);
+            if (active) fold.template run<V>(base + lo, lo, w0 + s0, w1, P, acc);
+            ring_release(rv, ring_stage(rv, base + lo + w1), rel);
+            w0 = w1;
+          }
+        }
+        part[r] = fold_vec<Op, V>(acc);
       }
-      const Acc a = lanes_allreduce<Op>(fold_vec<Op, V>(acc), 32);
-      if (lane == 0 && active) wsh[buf][m][warp] = a;
+      lanes_reduce_many<Op, kReduceBatch>(part, 32, lane);
+      const int k = lane / (32 / kReduceBatch);
+      if ((lane & (32 / kReduceBatch - 1)) == 0 && active && mb + k < mc) wsh[buf][mb + k][warp] = part[0];
     }
     consumer_sync();
     if (tid < mc) {
@@ -506,6 +555,50 @@ __device__ __forceinline__ void ring_lanes_items(const RingGeom& gm, const Fold&
   const int team = tid / L;
   const int64_t fit = kLanesWindowBytes / (4 * gm.R);
   const int per = static_cast<int>(fit >= teams ? (fit / teams) * teams : (fit > 0 ? fit : 1));
+  if (gm.G == 1) {
+    // one item per output, R < 2^13 iterations: phase-relative 32-bit offsets
+    typename Op::Out* outp = static_cast<typename Op::Out*>(bn.out) + item0;
+    const int32_t R = static_cast<int32_t>(gm.R);
+    for (int b = 0; b < count; b += per) {
+      const int n = (count - b < per) ? count - b : per;
+      const int64_t e0 = (item0 + b) * gm.R;
+      const int64_t e1 = e0 + static_cast<int64_t>(n) * R;
+      ring_wait(rv, e1, ready);
+      const uint32_t off = static_cast<uint32_t>(e0) * 4u + fold.shift;
+      if (L >= kReduceBatch) {
+        // kReduceBatch rounds, then one batched team reduction
+        constexpr int B = kReduceBatch;
+        for (int j0 = 0; j0 < n; j0 += B * teams) {   // the same trip count in every lane
+          Acc part[B];
+#pragma unroll
+          for (int r = 0; r < B; ++r) {
+            const int j = j0 + r * teams + team;
+            Acc acc[V];
+#pragma unroll
+            for (int i = 0; i < V; ++i) acc[i] = Op::ident();
+            if (j < n) fold.template run_at<V>(off + 4u * static_cast<uint32_t>(j * R), fold.w, s0, R, gm.P, acc);
+            part[r] = fold_vec<Op, V>(acc);
+          }
+          lanes_reduce_many<Op, B>(part, L, lt);
+          const int j = j0 + (lt / (L / B)) * teams + team;
+          if ((lt & (L / B - 1)) == 0 && j < n) outp[b + j] = Op::finish(part[0]);
+        }
+      } else {
+        for (int j0 = 0; j0 < n; j0 += teams) {   // the same trip count in every lane
+          const int j = j0 + team;
+          const bool valid = j < n;
+          Acc acc[V];
+#pragma unroll
+          for (int i = 0; i < V; ++i) acc[i] = Op::ident();
+          if (valid) fold.template run_at<V>(off + 4u * static_cast<uint32_t>(j * R), fold.w, s0, R, gm.P, acc);
+          const Acc a = lanes_allreduce<Op>(fold_vec<Op, V>(acc), L);
+          if (valid && lt == 0) outp[b + j] = Op::finish(a);
+        }
+      }
+      ring_release(rv, ring_stage(rv, e1), rel);
+    }
+    return;
+  }
   for (int b = 0; b < count; b += per) {
     const int n = (count - b < per) ? count - b : per;
     int64_t base, lo, hi;

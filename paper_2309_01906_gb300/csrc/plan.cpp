@@ -125,21 +125,27 @@ static void auto_map(const NestPlan& p, hp_level_map* m) {
   int64_t O = 1, R = 1;
   for (int l = 0; l < r; ++l) O *= p.ext[l];
   for (int l = r; l < d; ++l) R *= p.ext[l];
+  // Teams are sized so that every lane folds at least ~16 iterations of an
+  // output: below that, the team's reduction tree and per-output bookkeeping
+  // cost as much as the folds themselves.
   int red_hw;
   int sub = 0;
   if (R >= 4096) {
     red_hw = (O < 2 * kAssumedSMs && R >= 65536) ? HP_HW_GRID : HP_HW_CTA;
-  } else if (R >= 128) {
+  } else if (R >= 512) {
     red_hw = HP_HW_WARP;
-  } else if (R >= 8) {
+  } else if (R >= 32) {
     red_hw = HP_HW_SUBWARP;
     sub = 2;
-    while (sub < 16 && sub * 4 * 2 <= R) sub *= 2;
+    while (sub < 16 && sub * 2 * 16 <= R) sub *= 2;
+  } else if (R % 4 == 0) {
+    red_hw = HP_HW_LANE;   // one thread per output, 4 vector slots (128-bit loads)
+    sub = 4;
   } else {
     red_hw = HP_HW_SEQ;
   }
   // all reduced levels collapse into one contiguous virtual level
-  for (int l = r; l < d; ++l) m[l] = {red_hw, red_hw == HP_HW_SUBWARP ? sub : 0, 0};
+  for (int l = r; l < d; ++l) m[l] = {red_hw, red_hw == HP_HW_SUBWARP || red_hw == HP_HW_LANE ? sub : 0, 0};
   if (r == 0 && red_hw == HP_HW_SUBWARP) {
     // a single output: one sub-warp group would leave the rest of the warp idle
     for (int l = r; l < d; ++l) m[l] = {HP_HW_WARP, 0, 0};

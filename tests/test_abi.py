@@ -117,8 +117,11 @@ def test_auto_plans():
     assert plan([1024, 1024], 1)["team"] == "lanes"
     assert plan([64, 512, 16, 1024], 2)["team"] == "block"
     assert plan([2, 1 << 20], 1)["grid_parts"] > 1
-    assert plan([1000, 16], 1)["team_lanes"] in (2, 4, 8, 16)
+    # teams sized for about 16 iterations per lane of every output
+    assert plan([1000, 200], 1)["team_lanes"] == 8
+    assert plan([1000, 16], 1)["team_lanes"] == 1 and plan([1000, 16], 1)["vec"] == 4
     assert plan([1000, 3], 1)["team_lanes"] == 1
+    assert plan([1000, 512], 1)["team_lanes"] == 32
     assert plan([4, 5], 2)["team"] == "map"
 
 
