@@ -325,6 +325,77 @@ struct RingFold {
     }
     for (; x < x1; x += P) apply<V>(acc, load<V>(off, wp, x));
   }
+
+  // Fold two items together: the same iterations x = x0, x0 + P, ... < x1
+  // of items A and B, whose iteration 0 sits at ring bytes (before the mask)
+  // offA and offA + dist.  Each item sees exactly the operation sequence of
+  // run_at; the two chains are independent (twice the work in flight per
+  // thread) and, for FP32 sums of one slot, advance as packed FP32x2 pairs.
+  template <int V>
+  __device__ __forceinline__ void run_pair(uint32_t offA, uint32_t dist, int32_t x0, int32_t x1, int32_t P,
+                                           typename Op::Acc (&A)[V], typename Op::Acc (&B)[V]) const {
+    const uint32_t a0 = (offA + 4u * static_cast<uint32_t>(x0)) & static_cast<uint32_t>(kRingBytes - 1);
+    const In* wp = DOT ? w : nullptr;
+    if (x0 >= x1) return;
+    if (a0 + dist + 4u * static_cast<uint32_t>(x1 - x0) <= static_cast<uint32_t>(kRingBytes)) {
+      // neither item wraps around the end of the ring: linear addresses
+      const uint32_t step = 4u * static_cast<uint32_t>(P);
+      uint32_t pa = ring + a0;
+      for (int32_t x = x0; x < x1; x += P, pa += step) {
+        Vals<Op, V> va, vb;
+        if constexpr (V == 4) {
+          lds4(pa, va.a);
+          lds4(pa + dist, vb.a);
+        } else {
+#pragma unroll
+          for (int i = 0; i < V; ++i) {
+            lds1(pa + 4u * i, va.a[i]);
+            lds1(pa + dist + 4u * i, vb.a[i]);
+          }
+        }
+        if constexpr (DOT) load_w<V>(wp, x, va, vb);
+        apply2<V>(A, B, va, vb);
+      }
+    } else {
+      for (int32_t x = x0; x < x1; x += P) {
+        Vals<Op, V> va = load<V>(offA, wp, x), vb = load<V>(offA + dist, wp, x);
+        apply2<V>(A, B, va, vb);
+      }
+    }
+  }
+  template <int V>
+  __device__ __forceinline__ void load_w(const In* wp, int32_t x, Vals<Op, V>& va, Vals<Op, V>& vb) const {
+    if constexpr (V == 4) {
+      const auto r = ld_keep4(wp + x);
+      va.b[0] = vb.b[0] = r.x;
+      va.b[1] = vb.b[1] = r.y;
+      va.b[2] = vb.b[2] = r.z;
+      va.b[3] = vb.b[3] = r.w;
+    } else {
+#pragma unroll
+      for (int i = 0; i < V; ++i) va.b[i] = vb.b[i] = ld_keep(wp + x + i);
+    }
+  }
+  template <int V>
+  __device__ __forceinline__ void apply2(typename Op::Acc (&A)[V], typename Op::Acc (&B)[V], const Vals<Op, V>& va,
+                                         const Vals<Op, V>& vb) const {
+    if constexpr (V == 1 && std::is_same<Op, OpF32Comp>::value) {
+      float2 sp = make_float2(A[0].s, B[0].s), cp = make_float2(A[0].c, B[0].c);
+      if constexpr (DOT) comp_prod_pair(sp, cp, make_float2(va.a[0], vb.a[0]), make_float2(va.b[0], vb.b[0]));
+      else comp_add_pair(sp, cp, make_float2(va.a[0], vb.a[0]));
+      A[0] = {sp.x, cp.x};
+      B[0] = {sp.y, cp.y};
+    } else if constexpr (V == 1 && std::is_same<Op, OpF32Sum>::value) {
+      float2 sp = make_float2(A[0], B[0]);
+      if constexpr (DOT) sp = fma2(make_float2(va.a[0], vb.a[0]), make_float2(va.b[0], vb.b[0]), sp);
+      else sp = add2(sp, make_float2(va.a[0], vb.a[0]));
+      A[0] = sp.x;
+      B[0] = sp.y;
+    } else {
+      apply<V>(A, va);
+      apply<V>(B, vb);
+    }
+  }
 };
 
 // geometry of a streamed nest, in registers
@@ -565,34 +636,43 @@ __device__ __forceinline__ void ring_lanes_items(const RingGeom& gm, const Fold&
       const int64_t e1 = e0 + static_cast<int64_t>(n) * R;
       ring_wait(rv, e1, ready);
       const uint32_t off = static_cast<uint32_t>(e0) * 4u + fold.shift;
+      const uint32_t dist = 4u * static_cast<uint32_t>(teams * R);   // ring bytes between a team's rounds
       if (L >= kReduceBatch) {
-        // kReduceBatch rounds, then one batched team reduction
+        // kReduceBatch rounds (two pairs), then one batched team reduction
         constexpr int B = kReduceBatch;
         for (int j0 = 0; j0 < n; j0 += B * teams) {   // the same trip count in every lane
           Acc part[B];
 #pragma unroll
-          for (int r = 0; r < B; ++r) {
-            const int j = j0 + r * teams + team;
-            Acc acc[V];
+          for (int r = 0; r < B; r += 2) {
+            const int ja = j0 + r * teams + team, jb = ja + teams;
+            Acc accA[V], accB[V];
 #pragma unroll
-            for (int i = 0; i < V; ++i) acc[i] = Op::ident();
-            if (j < n) fold.template run_at<V>(off + 4u * static_cast<uint32_t>(j * R), fold.w, s0, R, gm.P, acc);
-            part[r] = fold_vec<Op, V>(acc);
+            for (int i = 0; i < V; ++i) accA[i] = accB[i] = Op::ident();
+            const uint32_t offA = off + 4u * static_cast<uint32_t>(ja * R);
+            if (jb < n) fold.template run_pair<V>(offA, dist, s0, R, gm.P, accA, accB);
+            else if (ja < n) fold.template run_at<V>(offA, fold.w, s0, R, gm.P, accA);
+            part[r] = fold_vec<Op, V>(accA);
+            part[r + 1] = fold_vec<Op, V>(accB);
           }
           lanes_reduce_many<Op, B>(part, L, lt);
           const int j = j0 + (lt / (L / B)) * teams + team;
           if ((lt & (L / B - 1)) == 0 && j < n) outp[b + j] = Op::finish(part[0]);
         }
       } else {
-        for (int j0 = 0; j0 < n; j0 += teams) {   // the same trip count in every lane
-          const int j = j0 + team;
-          const bool valid = j < n;
-          Acc acc[V];
+        for (int j0 = 0; j0 < n; j0 += 2 * teams) {   // the same trip count in every lane
+          const int ja = j0 + team, jb = ja + teams;
+          Acc accA[V], accB[V];
 #pragma unroll
-          for (int i = 0; i < V; ++i) acc[i] = Op::ident();
-          if (valid) fold.template run_at<V>(off + 4u * static_cast<uint32_t>(j * R), fold.w, s0, R, gm.P, acc);
-          const Acc a = lanes_allreduce<Op>(fold_vec<Op, V>(acc), L);
-          if (valid && lt == 0) outp[b + j] = Op::finish(a);
+          for (int i = 0; i < V; ++i) accA[i] = accB[i] = Op::ident();
+          const uint32_t offA = off + 4u * static_cast<uint32_t>(ja * R);
+          if (jb < n) fold.template run_pair<V>(offA, dist, s0, R, gm.P, accA, accB);
+          else if (ja < n) fold.template run_at<V>(offA, fold.w, s0, R, gm.P, accA);
+          const Acc a = lanes_allreduce<Op>(fold_vec<Op, V>(accA), L);
+          const Acc c = lanes_allreduce<Op>(fold_vec<Op, V>(accB), L);
+          if (lt == 0) {
+            if (ja < n) outp[b + ja] = Op::finish(a);
+            if (jb < n) outp[b + jb] = Op::finish(c);
+          }
         }
       }
       ring_release(rv, ring_stage(rv, e1), rel);
