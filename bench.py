@@ -494,7 +494,7 @@ def make_uneven_batch(n_nests, seed=9, tune=False, stream=None):
                 continue
             seen.add(key)
             n = hb.Nest(list(sh.extents), sh.red_level, sh.op, sh.prec, "load")
-            n.tune(ins[i], outs[i], sp)
+            n.tune(ins[i], outs[i], sp, batched=True)   # timed in the executor the nests run in
             n.close()
         tuned_classes = len(seen)
     nests = [hb.Nest(list(sh.extents), sh.red_level, sh.op, sh.prec, "load") for sh in shapes]

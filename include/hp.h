@@ -238,6 +238,11 @@ hp_status hp_nest_run_batch(hp_nest *const *nests, const void *const *const *in_
  * of the output count and of the reduced size, 128-bit divisibility, body,
  * precision, operator); nests created later with map == NULL take it.
  * flags bit 0: re-time even if the class is already tuned.
+ * flags bit 1: time every candidate, and the planner's own map, in the
+ *   batched executor (hp_nest_run_batch on as many copies of the nest as give
+ *   about 2^24 iterations, at most 64, all reading in_dev and writing the same
+ *   values to out_dev), keeping the planner's map unless another is 3% faster:
+ *   the choice for nests that will run in batches or under a server.
  * Synchronous (waits for the stream).  On return out_dev holds the installed
  * plan's result.  The GEOMETRIC body is not tuned.  Tune a nest before
  * passing it to hp_nest_run_batch or a server; batches built earlier with it

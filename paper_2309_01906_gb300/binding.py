@@ -232,9 +232,11 @@ class PreparedRun:
         _check(st, "hp_nest_run")
 
 
-def hp_nest_tune(nest, in_ptrs, out_ptr, stream=0, retime=False):
-    """Time candidate bindings on these buffers, install the fastest (synchronous)."""
-    st = lib().hp_nest_tune(nest, _ptr_array(in_ptrs), out_ptr or None, stream or None, 1 if retime else 0)
+def hp_nest_tune(nest, in_ptrs, out_ptr, stream=0, retime=False, batched=False):
+    """Time candidate bindings on these buffers, install the fastest (synchronous);
+    batched=True times them in the batched executor (flags bit 1)."""
+    flags = (1 if retime else 0) | (2 if batched else 0)
+    st = lib().hp_nest_tune(nest, _ptr_array(in_ptrs), out_ptr or None, stream or None, flags)
     _check(st, "hp_nest_tune")
 
 
@@ -325,8 +327,8 @@ class Nest:
     def run_host(self, in_ptrs, out_ptr, stream=0):
         hp_nest_run_host(self.handle, in_ptrs, out_ptr, stream)
 
-    def tune(self, in_ptrs, out_ptr, stream=0, retime=False):
-        hp_nest_tune(self.handle, in_ptrs, out_ptr, stream, retime)
+    def tune(self, in_ptrs, out_ptr, stream=0, retime=False, batched=False):
+        hp_nest_tune(self.handle, in_ptrs, out_ptr, stream, retime, batched)
 
     def describe(self) -> dict:
         return hp_nest_describe(self.handle)

@@ -102,7 +102,7 @@ struct LaunchCfg {
 // A tuned binding for a shape class (all reduced levels collapsed onto one
 // hardware level, outputs over the grid).
 struct TuneChoice {
-  int32_t red_hw = HP_HW_AUTO;  // hardware level of the reduced levels
+  int32_t red_hw = HP_HW_AUTO;  // hardware level of the reduced levels (AUTO: the planner's map)
   int32_t sub = 0;              // SUBWARP width, LANE vector slots, or CTA warps
   int64_t split_parts = 0;      // > 0: reduced levels split over this many grid parts
 };

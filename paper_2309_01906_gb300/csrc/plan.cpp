@@ -103,8 +103,15 @@ size_t tune_cache_size() {
   return g_tune.size();
 }
 
+static void auto_map(const NestPlan& p, hp_level_map* m);
+
 // outputs over the grid; every reduced level on the chosen hardware level
+// (HP_HW_AUTO: the planner's own map)
 void tune_apply(const NestPlan& p, const TuneChoice& c, hp_level_map* m) {
+  if (c.red_hw == HP_HW_AUTO) {
+    auto_map(p, m);
+    return;
+  }
   const int d = p.depth, r = p.red_level;
   int64_t R = 1;
   for (int l = r; l < d; ++l) R *= p.ext[l];

@@ -3,6 +3,10 @@
 // levels by what they provide and Sec. 3.3 compiles a region for several
 // candidate levels and picks one at run time; here the pick is measured).
 //
+// With flags bit 1 every candidate (and the planner's own map) is timed in the
+// batched executor, on as many copies of the nest as give about 2^24
+// iterations, and the planner's map is kept unless another one is 3% faster.
+//
 // Candidates keep the outputs on the grid and put every reduced level on one
 // hardware level: a CTA of 4 or 8 warps, a warp, a sub-warp group of 2..16
 // lanes, the 4 vector slots of one thread, one thread sequentially, or a split
@@ -24,11 +28,12 @@ hp_status tune_release_device(hp_nest* n);
 
 namespace {
 
-std::vector<TuneChoice> candidates(const NestPlan& p, int sms) {
+std::vector<TuneChoice> candidates(const NestPlan& p, int sms, bool with_auto) {
   int64_t O = 1, R = 1;
   for (int l = 0; l < p.red_level; ++l) O *= p.ext[l];
   for (int l = p.red_level; l < p.depth; ++l) R *= p.ext[l];
   std::vector<TuneChoice> c;
+  if (with_auto) c.push_back(TuneChoice{});   // the planner's own map first
   auto add = [&](int hw, int sub, int64_t parts) {
     TuneChoice t;
     t.red_hw = hw;
@@ -76,6 +81,35 @@ hp_status time_plan(hp_nest* tmp, const void* const* in_dev, void* out_dev, cuda
   return HP_OK;
 }
 
+// the same, in the batched executor: `copies` instances of the nest in one
+// hp_nest_run_batch (they read the same inputs and write the same, identical
+// outputs), so that a small nest is timed at the throughput it gets there
+hp_status time_plan_batched(hp_nest* tmp, const void* const* in_dev, void* out_dev, cudaStream_t st, int copies,
+                            float* ms) {
+  hp_status s = ensure_device(tmp);
+  if (s != HP_OK) return s;
+  std::vector<hp_nest*> ns(copies, tmp);
+  std::vector<const void* const*> ins(copies, in_dev);
+  std::vector<void*> outs(copies, out_dev);
+  if ((s = hp_nest_run_batch(ns.data(), ins.data(), outs.data(), copies, st)) != HP_OK) return s;  // builds the batch
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  constexpr int kReps = 3;
+  cudaEventRecord(e0, st);
+  for (int i = 0; i < kReps && s == HP_OK; ++i) s = hp_nest_run_batch(ns.data(), ins.data(), outs.data(), copies, st);
+  cudaEventRecord(e1, st);
+  const cudaError_t e = cudaEventSynchronize(e1);
+  float t = 0.0f;
+  if (e == cudaSuccess) cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != HP_OK) return s;
+  if (e != cudaSuccess) return fail(HP_ECUDA, std::string("tuning run: ") + cudaGetErrorString(e));
+  *ms = t / kReps;
+  return HP_OK;
+}
+
 }  // namespace
 }  // namespace hp
 
@@ -92,10 +126,15 @@ extern "C" hp_status hp_nest_tune(hp_nest* n, const void* const* in_dev, void* o
   const TuneKey key = tune_key(p);
   TuneChoice best;
   const bool reuse = (flags & 1) == 0;
+  const bool batched = (flags & 2) != 0;
+  // batched timing: enough copies for about 2^24 iterations (at most 64)
+  const int copies = static_cast<int>(std::min<int64_t>(64, std::max<int64_t>(1, ((int64_t(1) << 24) + p.total - 1) /
+                                                                                   std::max<int64_t>(1, p.total))));
   bool have = reuse && tune_lookup(key, &best);
   if (!have) {
     float best_ms = FLT_MAX;
-    const std::vector<TuneChoice> cand = candidates(p, n->sms);
+    float auto_ms = -1.0f;
+    const std::vector<TuneChoice> cand = candidates(p, n->sms, batched);
     for (const TuneChoice& c : cand) {
       hp_level_map m[HP_MAX_DEPTH];
       tune_apply(p, c, m);
@@ -110,18 +149,22 @@ extern "C" hp_status hp_nest_tune(hp_nest* n, const void* const* in_dev, void* o
       if (hp_nest_create(p.depth, p.ext, nullptr, 0, m, p.op, p.red_level, p.prec, p.body, params, &tmp) != HP_OK)
         continue;  // illegal for this shape
       float ms = 0.0f;
-      const hp_status ts = time_plan(tmp, in_dev, out_dev, st, &ms);
+      const hp_status ts = batched ? time_plan_batched(tmp, in_dev, out_dev, st, copies, &ms)
+                                   : time_plan(tmp, in_dev, out_dev, st, &ms);
       hp_nest_destroy(tmp);
       if (ts != HP_OK) {
         if (ts == HP_ECUDA) return ts;
         continue;
       }
+      if (c.red_hw == HP_HW_AUTO) auto_ms = ms;
       if (ms < best_ms) {
         best_ms = ms;
         best = c;
         have = true;
       }
     }
+    // batched: keep the planner's map unless another one is clearly faster
+    if (batched && auto_ms >= 0.0f && best_ms > 0.97f * auto_ms) best = TuneChoice{};
     if (!have) return fail(HP_EUNSUPPORTED, "no candidate binding runs for this shape");
     tune_store(key, best);
   }

@@ -10,9 +10,11 @@ from tests.hp_testutil import assert_close, oracle_rect
 pytestmark = pytest.mark.gpu
 
 
+@pytest.mark.parametrize("batched", [False, True])
 @pytest.mark.parametrize("ext,r,op,prec", [([200, 3000], 1, "sum", "f32_comp"), ([5000, 6], 1, "max", "i32"),
                                           ([3, 200000], 1, "sum", "f32"), ([64, 8, 100], 1, "sum", "i64")])
-def test_tune_installs_and_caches(ext, r, op, prec):
+def test_tune_installs_and_caches(ext, r, op, prec, batched):
+    # batched: candidates (and the planner's own map) timed in the batched executor
     import torch
     rng = np.random.Generator(np.random.PCG64(7))
     total = int(np.prod(ext))
@@ -27,7 +29,7 @@ def test_tune_installs_and_caches(ext, r, op, prec):
     out = torch.empty(O, dtype=dt, device="cuda")
     s = torch.cuda.current_stream().cuda_stream
     n = hb.Nest(ext, r, op, prec, "load")
-    n.tune([dA.data_ptr()], out.data_ptr(), s, retime=True)
+    n.tune([dA.data_ptr()], out.data_ptr(), s, retime=True, batched=batched)
     d = n.describe()
     assert d["tuned"]
     torch.cuda.synchronize()
