@@ -24,6 +24,9 @@ rflat = row-major index over the reduced levels r..d-1):
     dot_bcast  A[flat] * w[rflat]
     affine     a + b * (flat mod m)        params (a, b, m), integers
     geometric  fl32(q ** (flat mod m))     params (q, m), q**k formed in FP64
+
+Stencil nests with ghost zones (Sec. 2 stencils, Sec. 4 map sections) have
+their own oracle in ``oracle/stencil.py``.
 """
 from __future__ import annotations
 
