@@ -66,6 +66,24 @@ def abs_steps(A: np.ndarray, coeffs, radius: int, n_steps: int) -> np.ndarray:
     return steps(np.abs(np.asarray(A, dtype=np.float64)), np.abs(_coeffs(coeffs, radius)), radius, n_steps)
 
 
+def point(A: np.ndarray, coeffs, radius: int, n_steps: int, y: int, x: int) -> float:
+    """S^T(A)[y][x] from the window of half-width h = r*T around (y, x): a
+    point after T steps depends only on inputs within h (Sec. 2's tiling
+    argument).  Window points outside the array are 0 at every step, as in
+    ``steps``; window points inside it are updated, their own values being
+    exact wherever the centre can still see them."""
+    r, h = radius, radius * n_steps
+    ny, nx = A.shape
+    c = _coeffs(coeffs, r)
+    ys, xs = np.arange(y - h, y + h + 1), np.arange(x - h, x + h + 1)
+    inside = ((ys >= 0) & (ys < ny))[:, None] & ((xs >= 0) & (xs < nx))[None, :]
+    v = np.zeros((2 * h + 1, 2 * h + 1))
+    v[inside] = np.asarray(A, np.float64)[np.clip(ys, 0, ny - 1)][:, np.clip(xs, 0, nx - 1)][inside]
+    for _ in range(n_steps):
+        v = step(v, c, r) * inside
+    return float(v[h, h])
+
+
 def brute(A, coeffs, radius: int, n_steps: int):
     """Pure-Python loops (tiny arrays only)."""
     ny, nx = len(A), len(A[0])

@@ -84,6 +84,15 @@ def test_constant_field_is_conserved_away_from_the_edges():
     assert out[0, 0] < 3.0 - 0.5      # the zero ghost surface pulls the corner down
 
 
+@pytest.mark.parametrize("r,T", [(1, 1), (1, 3), (2, 2), (0, 2)])
+def test_point_equals_the_full_evaluation(r, T):
+    A, c = _rand((13, 17), 30 + r), _coeffs(r, 31 + T)
+    full = so.steps(A, c, r, T)
+    for y in range(13):
+        for x in range(17):
+            assert so.point(A, c, r, T, y, x) == pytest.approx(full[y, x], abs=1e-12)
+
+
 def test_abs_steps_bounds_the_result():
     A, c = _rand((18, 21), 9), _coeffs(1, 10)
     assert np.all(np.abs(so.steps(A, c, 1, 3)) <= so.abs_steps(A, c, 1, 3) + 1e-15)
