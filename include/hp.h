@@ -313,6 +313,61 @@ hp_status hp_serve_counters(const hp_server *s, uint64_t *completed, uint64_t *s
  * queued are dropped.  Nests and buffers stay the caller's. */
 void hp_serve_destroy(hp_server *s);
 
+/* ---------------------------------------------------------------------- */
+/* Stencil nests with ghost zones.
+ *
+ * Sec. 2: stencils can be tiled to any level that has local memory, a region
+ * chosen so that its input region fits that memory; Sec. 4: a level maps each
+ * of its units an array section, the `to` sections overlapping by a ghost
+ * surface, the `from` sections partitioning the array.
+ *
+ * One step of a 2-D stencil of radius r (0..4) over the ny x nx FP32 array v
+ * (row-major) is the cross-correlation
+ *     (S v)[y][x] = sum_{dy,dx = -r..r} c[dy+r][dx+r] * v[y+dy][x+dx],
+ * with v = 0 outside the array.  A nest of `steps` steps (1..8) computes
+ * S^steps(A), each point of each step as one FP32 fused multiply-add chain
+ * over the window in row-major (dy, dx) order, starting from 0, every step's
+ * values rounded to FP32: a run with steps = T gives bit for bit the result of
+ * T runs with steps = 1.
+ *
+ * Two levels: the GRID level's map sections (section_y x section_x points,
+ * whole tiles; 0 = the whole array) order the work, section after section, so
+ * that neighbouring tiles share their ghost rows through L2; the CTA level's
+ * tiles (tile_y x tile_x, tile_x a multiple of 4; 0 = automatic) are mapped
+ * into shared memory with a ghost border of r * steps points (one 2-D tensor
+ * copy, out-of-array points read as 0), all steps run there, and the CTA
+ * writes back its tile.
+ */
+typedef struct hp_stencil hp_stencil;
+typedef struct {
+  int64_t section_y, section_x;   /* GRID-level sections (multiples of the tile; 0 = whole array) */
+  int32_t tile_y, tile_x;         /* CTA-level tiles (0 = automatic) */
+} hp_stencil_map;
+
+/* Plan a stencil nest (host only, no GPU needed).  coeffs: (2r+1)^2 host
+ * floats, row-major over (dy, dx), copied.  map may be NULL (automatic).
+ * HP_EINVAL for sizes out of range or a tile whose ghost-bordered box does not
+ * fit one CTA's shared memory (226 KB) or one tensor copy (256 x 256 points). */
+hp_status hp_stencil_create(int64_t ny, int64_t nx, int radius, const float *coeffs, int steps,
+                            const hp_stencil_map *map, hp_stencil **out);
+
+/* Run on `stream` (asynchronous).  in_dev / out_dev: device arrays of ny x nx
+ * FP32, row-major, not overlapping.  Rows whose pitch (4 nx bytes) or base is
+ * not 16-byte aligned are loaded with plain loads instead of tensor copies
+ * (same results).  Device-side waits are bounded; hp_stencil_check reports. */
+hp_status hp_stencil_run(hp_stencil *s, const float *in_dev, float *out_dev, void *stream);
+
+/* The plan as one line of JSON: sizes, tile, ghost widths, tensor box,
+ * shared memory, tiles, and the GRID-level sections' `to` / `from` boxes
+ * (when there are at most 64 sections). */
+hp_status hp_stencil_describe(const hp_stencil *s, char *buf, size_t len);
+
+/* Wait for the stream, read the stencil's device error word (0 = none, 1 = a
+ * tensor-copy wait ran out of time); HP_ETIMEOUT if set. */
+hp_status hp_stencil_check(hp_stencil *s, void *stream, int32_t *device_error);
+
+void hp_stencil_destroy(hp_stencil *s);
+
 /*
  * Process-wide planner options, read when a nest is created (existing nests
  * keep their plan).  Names:

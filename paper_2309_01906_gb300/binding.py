@@ -40,7 +40,13 @@ EXPORTED = ["hp_nest_create", "hp_nest_run", "hp_nest_run_host", "hp_nest_run_st
             "hp_nest_tune", "hp_nest_error_bound",
             "hp_nest_describe", "hp_nest_check", "hp_nest_destroy", "hp_serve_create", "hp_serve_submit",
             "hp_serve_poll", "hp_serve_stats", "hp_serve_counters", "hp_serve_destroy", "hp_set_option", "hp_get_option",
-            "hp_last_error", "hp_version"]
+            "hp_last_error", "hp_version", "hp_stencil_create", "hp_stencil_run", "hp_stencil_describe",
+            "hp_stencil_check", "hp_stencil_destroy"]
+
+
+class hp_stencil_map(ctypes.Structure):
+    _fields_ = [("section_y", ctypes.c_int64), ("section_x", ctypes.c_int64), ("tile_y", ctypes.c_int32),
+                ("tile_x", ctypes.c_int32)]
 
 
 class hp_level_map(ctypes.Structure):
@@ -123,6 +129,17 @@ def lib() -> ctypes.CDLL:
         L.hp_set_option.argtypes = [ctypes.c_char_p, i64]
         L.hp_get_option.restype = i32
         L.hp_get_option.argtypes = [ctypes.c_char_p, ctypes.POINTER(i64)]
+        L.hp_stencil_create.restype = i32
+        L.hp_stencil_create.argtypes = [i64, i64, i32, ctypes.POINTER(ctypes.c_float), i32,
+                                        ctypes.POINTER(hp_stencil_map), ctypes.POINTER(p)]
+        L.hp_stencil_run.restype = i32
+        L.hp_stencil_run.argtypes = [p, p, p, p]
+        L.hp_stencil_describe.restype = i32
+        L.hp_stencil_describe.argtypes = [p, ctypes.c_char_p, ctypes.c_size_t]
+        L.hp_stencil_check.restype = i32
+        L.hp_stencil_check.argtypes = [p, p, ctypes.POINTER(ctypes.c_int32)]
+        L.hp_stencil_destroy.restype = None
+        L.hp_stencil_destroy.argtypes = [p]
         _lib = L
         return L
 
@@ -302,6 +319,69 @@ def hp_serve_counters(server):
 def hp_serve_destroy(server):
     if server:
         lib().hp_serve_destroy(server)
+
+
+def hp_stencil_create(ny, nx, radius, coeffs, steps, section=(0, 0), tile=(0, 0)):
+    """Plan a stencil nest (host only); coeffs: (2r+1)^2 floats, row-major over (dy, dx)."""
+    cs = [float(v) for v in coeffs]
+    if 0 <= radius <= 4 and len(cs) != (2 * radius + 1) ** 2:
+        raise HPError(HP_EINVAL, "hp_stencil_create", f"{(2 * radius + 1) ** 2} coefficients expected, got {len(cs)}")
+    arr = (ctypes.c_float * max(len(cs), 81))(*cs)   # the library reads (2r+1)^2 of them (r <= 4)
+    m = hp_stencil_map(section[0], section[1], tile[0], tile[1])
+    h = ctypes.c_void_p()
+    _check(lib().hp_stencil_create(ny, nx, radius, arr, steps, ctypes.byref(m), ctypes.byref(h)), "hp_stencil_create")
+    return h.value
+
+
+def hp_stencil_run(st, in_ptr, out_ptr, stream=0):
+    _check(lib().hp_stencil_run(st, in_ptr, out_ptr, stream or None), "hp_stencil_run")
+
+
+def hp_stencil_describe(st) -> dict:
+    buf = ctypes.create_string_buffer(16384)
+    _check(lib().hp_stencil_describe(st, buf, len(buf)), "hp_stencil_describe")
+    return json.loads(buf.value.decode())
+
+
+def hp_stencil_check(st, stream=0) -> int:
+    v = ctypes.c_int32()
+    status = lib().hp_stencil_check(st, stream or None, ctypes.byref(v))
+    if status not in (HP_OK, HP_ETIMEOUT):
+        _check(status, "hp_stencil_check")
+    return v.value
+
+
+def hp_stencil_destroy(st):
+    if st:
+        lib().hp_stencil_destroy(st)
+
+
+class Stencil:
+    """Convenience owner of one stencil handle."""
+
+    def __init__(self, ny, nx, radius, coeffs, steps=1, section=(0, 0), tile=(0, 0)):
+        self.handle = None
+        self.handle = hp_stencil_create(ny, nx, radius, coeffs, steps, section, tile)
+
+    def run(self, in_ptr, out_ptr, stream=0):
+        hp_stencil_run(self.handle, in_ptr, out_ptr, stream)
+
+    def describe(self) -> dict:
+        return hp_stencil_describe(self.handle)
+
+    def check(self, stream=0) -> int:
+        return hp_stencil_check(self.handle, stream)
+
+    def close(self):
+        if self.handle:
+            hp_stencil_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Nest:
