@@ -450,6 +450,59 @@ def run_gemv_workload(args):
                       "algorithmic_bytes": 4 * (1 << 20) + 2 * 4096}))
 
 
+# FP32 FMA peak derived from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
+FP32_FMA_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def run_stencil_workload(args):
+    """Stencil nest with ghost zones: 16384 x 16384 FP32 (seed 11), 9-point
+    diffusion stencil, zero ghost surface; steps 1 (HBM-bound) and 4 (steps fused
+    in shared memory, ghost border 4).  Inputs (1 GiB) are larger than L2."""
+    import torch
+
+    from paper_2309_01906_gb300 import binding as hb
+    from paper_2309_01906_gb300 import synth
+    ny = nx = args.stencil_n
+    r = 1
+    c = synth.DIFFUSION9
+    A = synth.stencil_f32(ny, nx)
+    dA = torch.from_numpy(A).cuda()
+    out = torch.empty_like(dA)
+    stream = torch.cuda.Stream()
+    peak, kind = measured_peaks()
+    res = {}
+    for T in [int(t) for t in args.stencil_steps.split(",")]:
+        st = hb.Stencil(ny, nx, r, c, T)
+        plan = st.describe()
+        plan.pop("sections", None)
+        ms = _event_time(lambda: st.run(dA.data_ptr(), out.data_ptr(), stream.cuda_stream), args.steps, args.warmup,
+                         stream)
+        assert st.check(stream.cuda_stream) == 0
+        st.close()
+        pts = ny * nx
+        gbs = 8 * pts / (ms * 1e-3) / 1e9
+        tflops = 2 * 9 * T * pts / (ms * 1e-3) / 1e12
+        res[f"steps_{T}"] = {
+            "ms": ms, "point_updates_per_s": pts * T / (ms * 1e-3), "plan": plan,
+            "roofline_hbm": {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak, "peak_kind": kind,
+                             "algorithmic_bytes": 8 * pts},
+            "roofline_alu": {"achieved": tflops, "peak": FP32_FMA_TFLOPS, "unit": "TFLOP/s",
+                             "frac": tflops / FP32_FMA_TFLOPS, "flops": 2 * 9 * T * pts,
+                             "peak_kind": "derived (152 SMs x 128 FP32 lanes x 2 x 2.07 GHz)"}}
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import stencil as so
+        sub = A[:1024, :1024].astype(np.float64)
+        t0 = time.perf_counter()
+        so.steps(sub, c, r, 1)
+        dt = time.perf_counter() - t0
+        cpu = {"value": sub.size / dt, "unit": "point updates/s", "cores": 1, "kind": "oracle",
+               "sample": "one step of the 9-point stencil on the 1024 x 1024 corner (FP64 numpy slices)"}
+    print(json.dumps({"workload": f"stencil nest {ny} x {nx} FP32, 9-point diffusion stencil, zero ghost surface",
+                      "metric": "stencil point updates/s", "steps": args.steps, "warmup": args.warmup,
+                      "results": res, "cpu_baseline": cpu, "l2": "inputs (1 GiB) larger than L2; no flush"}))
+
+
 def make_uneven_batch(n_nests, seed=9, tune=False, stream=None):
     """The batched workload: n_nests shapes drawn as in synth.uneven_shapes, their
     inputs packed into two device buffers (FP32 for sums, int32 for max), 16-byte
@@ -661,9 +714,11 @@ def main():
     ap.add_argument("--profile-b", type=int, default=0,
                     help="profiler case: run only the headline nest with this outer extent b")
     ap.add_argument("--prec", default="f32_comp", choices=["f32_comp", "f32"])
-    ap.add_argument("--workload", default="nest4", choices=["nest4", "csr", "gemv", "batch", "serve"],
+    ap.add_argument("--workload", default="nest4", choices=["nest4", "csr", "gemv", "batch", "serve", "stencil"],
                     help="nest4: the headline line; csr / gemv: measurement of the other workloads")
     ap.add_argument("--csr-rows", type=int, default=1 << 22)
+    ap.add_argument("--stencil-n", type=int, default=16384, help="stencil: array side")
+    ap.add_argument("--stencil-steps", default="1,4", help="stencil: steps per launch to time (comma list)")
     ap.add_argument("--batch-nests", type=int, default=10000)
     ap.add_argument("--batch-breakdown", action="store_true", help="batch: also time each plan class alone")
     ap.add_argument("--batch-class", default="", help="batch: keep only the nests of this plan class (e.g. lanes/1)")
@@ -681,6 +736,8 @@ def main():
         run_profile_case(args)
     elif args.workload == "csr":
         run_csr_workload(args)
+    elif args.workload == "stencil":
+        run_stencil_workload(args)
     elif args.workload == "gemv":
         run_gemv_workload(args)
     elif args.workload == "batch":

@@ -35,7 +35,6 @@ constexpr int kStencilMaxR = 4;
 constexpr int kStencilMaxSteps = 8;
 constexpr int kStencilBox = 256;                 // largest tensor-copy box side (points)
 constexpr size_t kStencilSmem = 226 * 1024;      // dynamic shared memory of one CTA (opt-in maximum less static use)
-constexpr int kStripRows = 8;                    // rows of one thread's column strip
 
 struct StencilPlan {
   int64_t ny = 0, nx = 0;
@@ -192,50 +191,104 @@ __device__ __noinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
   }
 }
 
-// rows [j0, j1) of buffer column i, step `final` or not: a sliding window of
-// 2R+1 rows x 2R+1 columns in registers, one new row per output point
-template <int R>
-__device__ __forceinline__ void column_strip(const float* __restrict__ src, float* __restrict__ dst,
-                                             const StencilArgs& a, int i, int j0, int j1, bool final, int64_t gy0,
-                                             int64_t gx0) {
+// N rows from j0 of buffer column i, inside the array: no per-point checks.
+// The strip's N + 2R input rows are loaded once each into a fully unrolled
+// register array and indexed (nothing is shifted).
+template <int R, int N>
+__device__ __forceinline__ void fast_strip(const float* __restrict__ src, float* __restrict__ dst,
+                                           const StencilArgs& a, int i, int j0, bool final, int64_t gy, int64_t gx) {
   constexpr int D = 2 * R + 1;
   const int P = a.boxW;
+  const float* sp = src + (j0 - R) * P + (i - R);
+  float v[N + 2 * R][D];
+#pragma unroll
+  for (int y = 0; y < N + 2 * R; ++y)
+#pragma unroll
+    for (int dx = 0; dx < D; ++dx) v[y][dx] = sp[y * P + dx];
+  float* dp = dst + j0 * P + i;
+  float* gp = a.out + (gy * a.nx + gx);
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int dy = 0; dy < D; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < D; ++dx) acc = __fmaf_rn(a.c[dy * D + dx], v[k + dy][dx], acc);
+    if (final) {
+      *gp = acc;
+      gp += a.nx;
+    } else {
+      *dp = acc;
+      dp += P;
+    }
+  }
+}
+
+// rows [j0, j0 + n) of buffer column i, any position: a sliding window of
+// 2R+1 rows x 2R+1 columns in registers and per-point array checks (points
+// outside the array: not stored in the last step, 0 in the others)
+template <int R, int S>
+__device__ __forceinline__ void checked_strip(const float* __restrict__ src, float* __restrict__ dst,
+                                              const StencilArgs& a, int i, int j0, int n, bool final, int64_t gy,
+                                              int64_t gx) {
+  constexpr int D = 2 * R + 1;
+  const int P = a.boxW;
+  const float* sp = src + (j0 - R) * P + (i - R);
   float w[D][D];
 #pragma unroll
   for (int dy = 1; dy < D; ++dy)
 #pragma unroll
-    for (int dx = 0; dx < D; ++dx) w[dy][dx] = src[(j0 - R + dy - 1) * P + i - R + dx];
-  const int64_t gx = gx0 + i;   // global column of buffer column i
+    for (int dx = 0; dx < D; ++dx) w[dy][dx] = sp[(dy - 1) * P + dx];
+  sp += (D - 1) * P;
   const bool col_in = gx >= 0 && gx < a.nx;
-  for (int j = j0; j < j1; ++j) {
+  float* dp = dst + j0 * P + i;
+  for (int k = 0; k < n; ++k) {
 #pragma unroll
     for (int dy = 0; dy < D - 1; ++dy)
 #pragma unroll
       for (int dx = 0; dx < D; ++dx) w[dy][dx] = w[dy + 1][dx];
 #pragma unroll
-    for (int dx = 0; dx < D; ++dx) w[D - 1][dx] = src[(j + R) * P + i - R + dx];
+    for (int dx = 0; dx < D; ++dx) w[D - 1][dx] = sp[dx];
+    sp += P;
     float acc = 0.0f;
 #pragma unroll
     for (int dy = 0; dy < D; ++dy)
 #pragma unroll
       for (int dx = 0; dx < D; ++dx) acc = __fmaf_rn(a.c[dy * D + dx], w[dy][dx], acc);
-    const int64_t gy = gy0 + j;
-    const bool in = col_in && gy >= 0 && gy < a.ny;
+    const bool in = col_in && gy + k >= 0 && gy + k < a.ny;
     if (final) {
-      if (in) a.out[gy * a.nx + gx] = acc;
+      if (in) a.out[(gy + k) * a.nx + gx] = acc;
     } else {
-      dst[j * P + i] = in ? acc : 0.0f;   // the zero ghost surface stays zero at every step
+      dp[k * P] = in ? acc : 0.0f;   // the zero ghost surface stays zero at every step
     }
   }
 }
 
-template <int R>
-__global__ void __launch_bounds__(kStencilThreads, 2)
+// one strip: rows [j0, j0 + n), n <= S; whole strips inside the array take
+// the check-free path
+template <int R, int S>
+__device__ __forceinline__ void strip(const float* __restrict__ src, float* __restrict__ dst, const StencilArgs& a,
+                                      int i, int j0, int n, bool final, int64_t gy0, int64_t gx0) {
+  const int64_t gx = gx0 + i, gy = gy0 + j0;
+  if (n == S && gx >= 0 && gx < a.nx && gy >= 0 && gy + S <= a.ny)
+    fast_strip<R, S>(src, dst, a, i, j0, final, gy, gx);
+  else
+    checked_strip<R, S>(src, dst, a, i, j0, n, final, gy, gx);
+}
+
+// FUSED: more than one step per launch (two buffers: 2 CTAs per SM at most,
+// so registers are spent on instruction-level parallelism); one step: radius
+// <= 1 keeps 4 CTAs per SM resident for memory-level parallelism
+#ifndef HP_STENCIL_STEP1_BLOCKS
+#define HP_STENCIL_STEP1_BLOCKS 3   // resident CTAs per SM the one-step kernels' registers are sized for (measured best)
+#endif
+template <int R, bool FUSED>
+__global__ void __launch_bounds__(kStencilThreads, R >= 4 ? 1 : ((R >= 2 || FUSED) ? 2 : HP_STENCIL_STEP1_BLOCKS))
     stencil_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ StencilArgs a) {
   extern __shared__ __align__(128) float sbuf[];
   __shared__ __align__(8) unsigned long long bar_word;
   __shared__ int ok_flag;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x;
   const uint32_t bar = smem_addr(&bar_word);
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
@@ -290,13 +343,15 @@ __global__ void __launch_bounds__(kStencilThreads, 2)
       const int e = a.h - R * s;
       const int jl = a.h - e, jh = a.h + a.TY + e;
       const int il = a.hx - e, ih = a.hx + a.TX + e;
-      const int n_cg = (ih - il + 31) / 32, n_rs = (jh - jl + kStripRows - 1) / kStripRows;
+      // (column, strip) items, columns fastest: every lane busy, neighbouring lanes on
+      // neighbouring columns; strips of S rows, the last one shorter
+      constexpr int S = R <= 1 ? 16 : (R == 2 ? 8 : 4);   // S + 2R rows of 2R+1 registers
+      const int H = jh - jl, W = ih - il, n_rs = (H + S - 1) / S;
       const bool final = s == a.T;
-      for (int q = warp; q < n_cg * n_rs; q += kStencilThreads / 32) {
-        const int cg = q % n_cg, rs = q / n_cg;
-        const int i = il + cg * 32 + lane;
-        const int j0 = jl + rs * kStripRows, j1 = min(jh, j0 + kStripRows);
-        if (i < ih) column_strip<R>(src, dst, a, i, j0, j1, final, gy0, gx0);
+      for (int q = tid; q < W * n_rs; q += kStencilThreads) {
+        const int rs = q / W, i = il + (q - rs * W);
+        const int j0 = jl + rs * S, n = min(S, jh - j0);
+        strip<R, S>(src, dst, a, i, j0, n, final, gy0, gx0);
       }
       __syncthreads();
     }
@@ -324,24 +379,30 @@ hp_status stencil_cuda_fail(cudaError_t e, const char* what) {
   return fail(HP_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-template <int R>
+template <int R, bool FUSED>
 cudaError_t stencil_prepare_kernel() {
-  static const cudaError_t e = cudaFuncSetAttribute(stencil_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                    static_cast<int>(kStencilSmem));
+  static const cudaError_t e = cudaFuncSetAttribute(
+      stencil_kernel<R, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kStencilSmem));
   return e;
+}
+
+template <int R, bool FUSED>
+cudaError_t stencil_launch_as(const CUtensorMap& tmap, const StencilArgs& a, size_t smem, int sms, cudaStream_t st) {
+  cudaError_t e = stencil_prepare_kernel<R, FUSED>();
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stencil_kernel<R, FUSED>, kStencilThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int grid = static_cast<int>(std::min<int64_t>(a.n_tiles, static_cast<int64_t>(per_sm) * sms));
+  stencil_kernel<R, FUSED><<<grid, kStencilThreads, smem, st>>>(tmap, a);
+  return cudaPeekAtLastError();
 }
 
 template <int R>
 cudaError_t stencil_launch(const CUtensorMap& tmap, const StencilArgs& a, size_t smem, int sms, cudaStream_t st) {
-  cudaError_t e = stencil_prepare_kernel<R>();
-  if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stencil_kernel<R>, kStencilThreads, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const int grid = static_cast<int>(std::min<int64_t>(a.n_tiles, static_cast<int64_t>(per_sm) * sms));
-  stencil_kernel<R><<<grid, kStencilThreads, smem, st>>>(tmap, a);
-  return cudaPeekAtLastError();
+  return a.T > 1 ? stencil_launch_as<R, true>(tmap, a, smem, sms, st)
+                 : stencil_launch_as<R, false>(tmap, a, smem, sms, st);
 }
 
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,

@@ -102,6 +102,15 @@ def nest4_f32(b: int = 64, i: int = 512, j: int = 16, k: int = 1024, seed_a: int
     return A, w
 
 
+def stencil_f32(ny: int = 16384, nx: int = 16384, seed: int = 11) -> np.ndarray:
+    """The stencil workload's array: FP32 uniform[-1, 1], row-major ny x nx."""
+    return uniform_f32(ny * nx, -1.0, 1.0, seed).reshape(ny, nx)
+
+
+# 9-point diffusion stencil (weights sum to 1): the stencil workload's coefficients
+DIFFUSION9 = [0.025, 0.1, 0.025, 0.1, 0.5, 0.1, 0.025, 0.1, 0.025]
+
+
 def zipf_lengths(n_rows: int, alpha: float = 1.5, max_len: int = 65536, seed: int = 5) -> np.ndarray:
     """Row lengths Zipf(alpha) drawn, then clipped to [1, max_len]."""
     def draw(g, o):
