@@ -503,6 +503,46 @@ def run_stencil_workload(args):
                       "results": res, "cpu_baseline": cpu, "l2": "inputs (1 GiB) larger than L2; no flush"}))
 
 
+def run_ordered_workload(args):
+    """Ordered reduction with a non-commutative operator: 64 rows of 2^22 affine
+    maps (a uniform [0.9, 1) seed 12, b normal seed 13), each row composed in
+    iteration order (the last value of y = a y + b from 0, and the product of a).
+    Inputs (2 GiB) are larger than L2."""
+    import torch
+
+    from paper_2309_01906_gb300 import binding as hb
+    from paper_2309_01906_gb300 import synth
+    O, R = args.ordered_rows, args.ordered_len
+    a = synth.uniform_f32(O * R, 0.9, 1.0, 12)
+    b = synth.normal_f32(O * R, 13)
+    da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    out = torch.empty(2 * O, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.Stream()
+    n = hb.Nest([O, R], 1, "compose", "f32", "load")
+    plan = n.describe()
+    ms = _event_time(lambda: n.run([da.data_ptr(), db.data_ptr()], out.data_ptr(), stream.cuda_stream), args.steps,
+                     args.warmup, stream)
+    n.close()
+    peak, kind = measured_peaks()
+    nbytes = 8 * O * R + 8 * O
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import ordered as oo
+        m = min(R, 1 << 20)
+        t0 = time.perf_counter()
+        oo.compose(a[:m].astype(np.float64), b[:m].astype(np.float64))
+        dt = time.perf_counter() - t0
+        cpu = {"value": m / dt, "unit": "iterations/s", "cores": 1, "kind": "oracle",
+               "sample": f"the first {m} maps of row 0, folded in FP64"}
+    print(json.dumps({"workload": f"ordered reduction {O} x {R}: composition of affine maps in iteration order",
+                      "metric": "nest iterations/s", "value": O * R / (ms * 1e-3), "unit": "iterations/s",
+                      "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup, "plan": plan,
+                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                                   "peak_kind": kind, "algorithmic_bytes": nbytes},
+                      "cpu_baseline": cpu, "l2": "inputs (2 GiB) larger than L2; no flush"}))
+
+
 def make_uneven_batch(n_nests, seed=9, tune=False, stream=None):
     """The batched workload: n_nests shapes drawn as in synth.uneven_shapes, their
     inputs packed into two device buffers (FP32 for sums, int32 for max), 16-byte
@@ -714,10 +754,12 @@ def main():
     ap.add_argument("--profile-b", type=int, default=0,
                     help="profiler case: run only the headline nest with this outer extent b")
     ap.add_argument("--prec", default="f32_comp", choices=["f32_comp", "f32"])
-    ap.add_argument("--workload", default="nest4", choices=["nest4", "csr", "gemv", "batch", "serve", "stencil"],
+    ap.add_argument("--workload", default="nest4", choices=["nest4", "csr", "gemv", "batch", "serve", "stencil", "ordered"],
                     help="nest4: the headline line; csr / gemv: measurement of the other workloads")
     ap.add_argument("--csr-rows", type=int, default=1 << 22)
     ap.add_argument("--stencil-n", type=int, default=16384, help="stencil: array side")
+    ap.add_argument("--ordered-rows", type=int, default=64, help="ordered: rows (outputs)")
+    ap.add_argument("--ordered-len", type=int, default=1 << 22, help="ordered: maps per row")
     ap.add_argument("--stencil-steps", default="1,4", help="stencil: steps per launch to time (comma list)")
     ap.add_argument("--batch-nests", type=int, default=10000)
     ap.add_argument("--batch-breakdown", action="store_true", help="batch: also time each plan class alone")
@@ -736,6 +778,8 @@ def main():
         run_profile_case(args)
     elif args.workload == "csr":
         run_csr_workload(args)
+    elif args.workload == "ordered":
+        run_ordered_workload(args)
     elif args.workload == "stencil":
         run_stencil_workload(args)
     elif args.workload == "gemv":

@@ -78,8 +78,29 @@ typedef enum hp_red_op {
     HP_RED_SUM = 0,
     HP_RED_MAX = 1,
     HP_RED_MIN = 2,
-    HP_RED_HIST_COUNT = 3   /* CSR nests only: count histogram of col >> shift */
+    HP_RED_HIST_COUNT = 3,  /* CSR nests only: count histogram of col >> shift */
+    HP_RED_AFFINE_COMPOSE = 4  /* non-commutative: composition of affine maps in
+                                  iteration order (below) */
 } hp_red_op;
+
+/*
+ * HP_RED_AFFINE_COMPOSE (Sec. 2: a reduction combines the results of sibling
+ * tasks on each level; OpenMP's reduction clause does not allow
+ * non-commutative user-defined operators, a hierarchy that combines siblings in
+ * order does).  Rectangular nests, prec HP_F32, body HP_BODY_LOAD with
+ * in_dev = {a, b}, two FP32 arrays of the nest's shape.  Iteration x of an
+ * output contributes f_x(y) = a[x] * y + b[x]; the output is the composition in
+ * iteration order F = f_{R-1} o ... o f_0, written as the pair (A, B) with
+ * F(y) = A * y + B: B is the last value of the recurrence y_x = a_x y_{x-1} + b_x
+ * from y = 0, A the product of the a_x.  out_dev: 2 floats per output (A, B).
+ * Every thread folds a contiguous range of iterations (A <- a A, B <- fma(a, B,
+ * b)); lanes, warps and grid parts are combined in iteration order: (A2, B2)
+ * after (A1, B1) gives (A2 A1, fma(A2, B1, B2)).  Level map: outputs on GRID,
+ * the reduced levels on WARP (a warp per output), CTA (sub_width warps per
+ * output) or GRID (tile > 0 on the first reduced level: parts of tile x the
+ * deeper extents, one CTA each, folded in part order), or AUTO.  Not batched,
+ * served, tuned or run from host buffers (HP_EUNSUPPORTED).
+ */
 
 /*
  * Arithmetic of body and reduction.

@@ -52,6 +52,9 @@ hp_status ensure_device(hp_nest* n) {
       e = cudaMemcpy(n->geo, n->plan.geo_table.data(), b, cudaMemcpyHostToDevice);
       if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy (geometric table)");
     }
+  } else if (n->kind == NEST_ORDERED) {
+    hp_status st = ordered_prepare(n);
+    if (st != HP_OK) return st;
   } else {
     hp_status st = csr_prepare(n);
     if (st != HP_OK) return st;
@@ -97,6 +100,12 @@ hp_status run_rect_with(hp_nest* n, const void* const* in_dev, void* out_dev, vo
 
 double error_bound(const hp_nest* n) {
   if (n->kind == NEST_RECT) return error_bound_rect(n->plan);
+  if (n->kind == NEST_ORDERED) {
+    // gamma_{2k}: every iteration passes through at most k folds or combines, each
+    // rounding one product and one fused multiply-add
+    const double u = std::ldexp(1.0, -24), k2 = 2.0 * n->ord.k;
+    return k2 * u / (1.0 - k2 * u);
+  }
   if (n->csr.op != HP_RED_SUM || n->csr.prec != HP_F32_COMP) return n->csr.op == HP_RED_SUM ? 1e-5 : 0.0;
   return 1e-6;
 }
@@ -119,6 +128,7 @@ hp_status tune_release_device(hp_nest* n) {
 
 size_t out_bytes(const hp_nest* n) {
   if (n->kind == NEST_RECT) return static_cast<size_t>(n->plan.rp.O) * n->plan.out_elem_bytes;
+  if (n->kind == NEST_ORDERED) return static_cast<size_t>(n->ord.O) * 2 * sizeof(float);
   return csr_out_bytes(n);
 }
 
@@ -167,7 +177,10 @@ hp_status hp_nest_create(int depth, const int64_t* extents, const int64_t* csr_o
   if (!n) return fail(HP_ENOMEM, "host allocation failed");
   std::string why;
   hp_status st;
-  if (csr_offsets != nullptr || body == HP_BODY_CSR_GATHER || op == HP_RED_HIST_COUNT) {
+  if (op == HP_RED_AFFINE_COMPOSE) {
+    n->kind = NEST_ORDERED;
+    st = plan_ordered(depth, extents, map, op, red_level, prec, body, &n->ord, &why);
+  } else if (csr_offsets != nullptr || body == HP_BODY_CSR_GATHER || op == HP_RED_HIST_COUNT) {
     n->kind = NEST_CSR;
     st = plan_csr(depth, n_rows, map, op, red_level, prec, body, body_params, &n->csr, &why);
   } else {
@@ -190,6 +203,7 @@ hp_status hp_nest_run(hp_nest* n, const void* const* in_dev, void* out_dev, void
   if (st != HP_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (n->kind == NEST_RECT) return run_rect(n, in_dev, out_dev, s);
+  if (n->kind == NEST_ORDERED) return run_ordered(n, in_dev, out_dev, s);
   return run_csr(n, in_dev, out_dev, s);
 }
 
@@ -248,7 +262,9 @@ hp_status hp_nest_error_bound(const hp_nest* n, double* rel_bound) {
 
 hp_status hp_nest_describe(const hp_nest* n, char* buf, size_t len) {
   if (!n || !buf || len == 0) return fail(HP_EINVAL, "NULL argument");
-  const std::string s = n->kind == NEST_RECT ? describe_plan(n->plan) : describe_csr(n->csr);
+  const std::string s = n->kind == NEST_RECT      ? describe_plan(n->plan)
+                        : n->kind == NEST_ORDERED ? describe_ordered(n->ord)
+                                                  : describe_csr(n->csr);
   const size_t k = s.size() < len - 1 ? s.size() : len - 1;
   std::memcpy(buf, s.data(), k);
   buf[k] = 0;
@@ -283,6 +299,7 @@ void hp_nest_destroy(hp_nest* n) {
     for (int i = 0; i < 2; ++i)
       if (n->stage_in[i]) cudaFree(n->stage_in[i]);
     if (n->stage_out) cudaFree(n->stage_out);
+    if (n->tickets) cudaFree(n->tickets);
     csr_release(n);
   }
   delete n;

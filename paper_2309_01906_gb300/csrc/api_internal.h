@@ -8,7 +8,7 @@
 #include "hp_internal.h"
 
 namespace hp {
-enum NestKind : int { NEST_RECT = 0, NEST_CSR = 1 };
+enum NestKind : int { NEST_RECT = 0, NEST_CSR = 1, NEST_ORDERED = 2 };
 struct CsrState;
 }  // namespace hp
 
@@ -16,6 +16,8 @@ struct hp_nest {
   int kind = hp::NEST_RECT;
   hp::NestPlan plan;          // rectangular nests
   hp::CsrPlan csr;            // CSR nests
+  hp::OrderedPlan ord;        // nests with an ordered (non-commutative) reduction
+  int32_t* tickets = nullptr; // per output, ordered nests split over grid parts
   hp::LaunchCfg cfg;
   int device = -1;            // device of the first run; -1 before it
   int sms = 0;
@@ -48,4 +50,11 @@ hp_status csr_prepare(hp_nest* n);
 hp_status run_csr(hp_nest* n, const void* const* in_dev, void* out_dev, cudaStream_t st);
 size_t csr_out_bytes(const hp_nest* n);
 void csr_release(hp_nest* n);
+
+// ordered reductions (ordered.cu)
+hp_status plan_ordered(int depth, const int64_t* extents, const hp_level_map* map, hp_red_op op, int red_level,
+                       hp_prec prec, hp_body body, OrderedPlan* out, std::string* why);
+std::string describe_ordered(const OrderedPlan& p);
+hp_status ordered_prepare(hp_nest* n);
+hp_status run_ordered(hp_nest* n, const void* const* in_dev, void* out_dev, cudaStream_t st);
 }  // namespace hp

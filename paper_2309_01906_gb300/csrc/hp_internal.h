@@ -99,6 +99,24 @@ struct LaunchCfg {
   int M = 1;           // items per round of a block team
 };
 
+// Plan of a nest with an ordered (non-commutative) reduction: outputs over the
+// grid, each output's reduced range [0, R) (contiguous) cut into G parts of
+// `part` iterations, a part folded by a team of `threads` threads, each thread
+// a contiguous block of `chunk` iterations.
+struct OrderedPlan {
+  int depth = 0, red_level = 0;
+  int64_t ext[HP_MAX_DEPTH] = {0};
+  hp_level_map map[HP_MAX_DEPTH] = {};
+  bool auto_map = false;
+  int64_t O = 0, R = 0;       // outputs, iterations per output
+  int32_t team = 0;           // 0: a warp per output; 1: a CTA of W warps per part
+  int32_t W = 8;              // warps per CTA team
+  int64_t G = 1, part = 0;    // grid parts per output, iterations per part
+  int64_t chunk = 0;          // iterations per thread (a multiple of 4 when V == 4)
+  int32_t V = 1;              // 4: 128-bit loads (R and part multiples of 4)
+  int32_t k = 0;              // longest chain of folds and combines of one iteration
+};
+
 // A tuned binding for a shape class (all reduced levels collapsed onto one
 // hardware level, outputs over the grid).
 struct TuneChoice {

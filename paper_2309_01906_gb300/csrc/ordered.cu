@@ -1,0 +1,331 @@
+// ordered.cu — nests with an ordered, non-commutative reduction
+// (HP_RED_AFFINE_COMPOSE: composition of affine maps in iteration order).
+//
+// Sec. 2: a reduction combines on each level the results of its sibling
+// tasks; with a non-commutative operator the siblings must be combined in the
+// order of the iterations they folded.  The lowering therefore gives every
+// thread a contiguous block of iterations (not the cyclic slots of the other
+// reductions), folds it sequentially, and combines lanes, warps and grid parts
+// by rank: an xor butterfly whose masks grow 1, 2, ..., 16 combines at each
+// level two adjacent ranks, the lower one first (Sec. 3.7's sibling exchange),
+// and the parts of an output are folded in part order by the CTA that takes
+// the last ticket.  Element x contributes f_x(y) = a_x y + b_x; a thread's
+// running pair (A, B) takes A <- a A, B <- fma(a, B, b); two adjacent ranges,
+// (A1, B1) then (A2, B2), combine to (A2 A1, fma(A2, B1, B2)).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <sstream>
+#include <string>
+
+#include "api_internal.h"
+
+namespace hp {
+
+constexpr int kOrdThreads = 256;
+
+namespace {
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace
+
+hp_status plan_ordered(int depth, const int64_t* extents, const hp_level_map* map, hp_red_op op, int red_level,
+                       hp_prec prec, hp_body body, OrderedPlan* out, std::string* why) {
+  auto bad = [&](const std::string& m) {
+    *why = m;
+    return HP_EINVAL;
+  };
+  if (op != HP_RED_AFFINE_COMPOSE) return bad("not an ordered reduction");
+  if (depth < 1 || depth > HP_MAX_DEPTH) return bad("depth must be in [1, HP_MAX_DEPTH]");
+  if (!extents) return bad("extents is NULL");
+  if (red_level < 0 || red_level >= depth) return bad("red_level must be in [0, depth - 1] (something is reduced)");
+  if (prec != HP_F32) return bad("HP_RED_AFFINE_COMPOSE takes prec HP_F32");
+  if (body != HP_BODY_LOAD) return bad("HP_RED_AFFINE_COMPOSE takes body HP_BODY_LOAD with inputs {a, b}");
+  OrderedPlan p;
+  p.depth = depth;
+  p.red_level = red_level;
+  int64_t O = 1, R = 1, inner = 1;
+  for (int l = 0; l < depth; ++l) {
+    if (extents[l] < 0) return bad("extents must be >= 0");
+    p.ext[l] = extents[l];
+    const int64_t e = std::max<int64_t>(extents[l], 1);
+    if (l < red_level) O = O * extents[l];
+    else R = R * extents[l];
+    if (l > red_level) inner *= e;
+    if (O > (int64_t(1) << 40) || R > (int64_t(1) << 40)) return bad("nest too large");
+  }
+  if (O * std::max<int64_t>(R, 1) > (int64_t(1) << 40)) return bad("nest too large (2^40 iterations)");
+  p.O = O;
+  p.R = R;
+  bool all_auto = map == nullptr;
+  if (map) {
+    all_auto = true;
+    for (int l = 0; l < depth; ++l)
+      if (map[l].hw != HP_HW_AUTO) all_auto = false;
+  }
+  p.auto_map = all_auto;
+  int red_hw = HP_HW_AUTO, sub = 0;
+  int64_t tile = 0;
+  if (!all_auto) {
+    for (int l = 0; l < red_level; ++l)
+      if (map[l].hw != HP_HW_GRID) return bad("ordered reductions keep their output levels on GRID");
+    red_hw = map[red_level].hw;
+    sub = map[red_level].sub_width;
+    tile = map[red_level].tile;
+    for (int l = red_level; l < depth; ++l)
+      if (map[l].hw != red_hw) return bad("the reduced levels of an ordered reduction share one hardware level");
+    if (red_hw != HP_HW_WARP && red_hw != HP_HW_CTA && red_hw != HP_HW_GRID)
+      return bad("ordered reductions put their reduced levels on WARP, CTA or GRID");
+    if (red_hw == HP_HW_CTA && (sub < 0 || sub > 32)) return bad("CTA sub_width must be in [0, 32]");
+    if (tile < 0) return bad("tile must be >= 0");
+  } else {
+    // a warp per output for short ranges, a CTA for long ones, grid parts when
+    // few outputs face a long range
+    red_hw = R <= 1024 ? HP_HW_WARP : ((O >= 304 || R <= 65536) ? HP_HW_CTA : HP_HW_GRID);
+  }
+  if (red_hw == HP_HW_WARP) {
+    p.team = 0;
+    p.W = 1;
+    p.G = 1;
+    p.part = R;
+  } else {
+    p.team = 1;
+    p.W = (red_hw == HP_HW_CTA && sub > 0) ? sub : 8;
+    if (red_hw == HP_HW_GRID) {
+      int64_t part;
+      if (tile > 0) {
+        part = tile * inner;
+      } else {
+        // about 8 CTA teams per SM over all parts (2 waves of 4 resident CTAs)
+        const int64_t want = std::max<int64_t>(1, ceil_div(8 * 152, std::max<int64_t>(O, 1)));
+        part = std::max<int64_t>(16384, ceil_div(R, want));
+        // whole iterations of the first reduced level, and 4-aligned parts (128-bit loads) when R allows
+        const int64_t step = (R % 4 == 0) ? inner * 4 / std::__gcd<int64_t>(inner, 4) : inner;
+        part = ceil_div(part, step) * step;
+      }
+      p.part = std::max<int64_t>(1, part);
+      p.G = R > 0 ? ceil_div(R, p.part) : 1;
+      if (p.G > (int64_t(1) << 30)) return bad("too many grid parts");
+    } else {
+      p.G = 1;
+      p.part = R;
+    }
+  }
+  for (int l = 0; l < depth; ++l)
+    p.map[l] = {l < red_level ? HP_HW_GRID : red_hw, l >= red_level && red_hw == HP_HW_CTA ? p.W : 0,
+                l == red_level && red_hw == HP_HW_GRID ? p.part / inner : 0};
+  const int64_t threads = p.team == 0 ? 32 : 32 * static_cast<int64_t>(p.W);
+  p.V = (R % 4 == 0 && p.part % 4 == 0) ? 4 : 1;
+  p.chunk = std::max<int64_t>(1, ceil_div(std::max<int64_t>(p.part, 1), threads));
+  if (p.V == 4) p.chunk = ceil_div(p.chunk, 4) * 4;
+  // longest chain: the thread's block, 5 lane levels, 5 warp levels (CTA teams), the part fold
+  p.k = static_cast<int32_t>(std::min<int64_t>(p.chunk + 5 + (p.team ? 5 : 0) + (p.G - 1), int64_t(1) << 30));
+  *out = p;
+  return HP_OK;
+}
+
+std::string describe_ordered(const OrderedPlan& p) {
+  static const char* hw[] = {"grid", "cluster", "cta", "warp", "subwarp", "lane", "seq", "auto"};
+  std::ostringstream s;
+  s << "{\"kind\":\"ordered\",\"op\":\"affine_compose\",\"depth\":" << p.depth << ",\"red_level\":" << p.red_level
+    << ",\"extents\":[";
+  for (int l = 0; l < p.depth; ++l) s << (l ? "," : "") << p.ext[l];
+  s << "],\"map\":[";
+  for (int l = 0; l < p.depth; ++l)
+    s << (l ? "," : "") << "{\"hw\":\"" << hw[p.map[l].hw] << "\",\"sub_width\":" << p.map[l].sub_width
+      << ",\"tile\":" << p.map[l].tile << "}";
+  s << "],\"auto_map\":" << (p.auto_map ? "true" : "false") << ",\"team\":\"" << (p.team ? "block" : "warp")
+    << "\",\"outputs\":" << p.O << ",\"reduced\":" << p.R << ",\"warps\":" << p.W << ",\"grid_parts\":" << p.G
+    << ",\"part\":" << p.part << ",\"chunk\":" << p.chunk << ",\"vec\":" << p.V << ",\"chain\":" << p.k
+    << ",\"kernel\":\"ordered_" << (p.team ? "block" : "warp") << "\"}";
+  return s.str();
+}
+
+namespace {
+
+struct OrdArgs {
+  const float* a;
+  const float* b;
+  float* out;
+  float2* part;       // (A, B) of every (output, part) when G > 1
+  int32_t* tickets;   // per output, G > 1
+  int64_t O, R, G, part_len, chunk;
+  int32_t W;
+};
+
+// (A1, B1) then (A2, B2): the later map applied after the earlier one
+__device__ __forceinline__ float2 compose(float2 e, float2 l) {
+  return make_float2(__fmul_rn(l.x, e.x), __fmaf_rn(l.x, e.y, l.y));
+}
+
+// fold iterations [s, e) of the maps (a, b) into (A, B), in order
+template <int V>
+__device__ __forceinline__ float2 fold_block(const float* __restrict__ a, const float* __restrict__ b, int64_t s,
+                                             int64_t e, float2 v) {
+  if constexpr (V == 4) {
+    // four 128-bit loads of each input in flight; L1-cached, because a lane
+    // walks its own lines (neighbouring lanes are a block apart) and every
+    // line serves 8 of its loads
+    for (; s + 16 <= e; s += 16) {
+      float4 av[4], bv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        av[q] = __ldg(reinterpret_cast<const float4*>(a + s + 4 * q));
+        bv[q] = __ldg(reinterpret_cast<const float4*>(b + s + 4 * q));
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        v = compose(v, make_float2(av[q].x, bv[q].x));
+        v = compose(v, make_float2(av[q].y, bv[q].y));
+        v = compose(v, make_float2(av[q].z, bv[q].z));
+        v = compose(v, make_float2(av[q].w, bv[q].w));
+      }
+    }
+    for (; s < e; s += 4) {
+      const float4 a0 = __ldg(reinterpret_cast<const float4*>(a + s));
+      const float4 b0 = __ldg(reinterpret_cast<const float4*>(b + s));
+      v = compose(v, make_float2(a0.x, b0.x));
+      v = compose(v, make_float2(a0.y, b0.y));
+      v = compose(v, make_float2(a0.z, b0.z));
+      v = compose(v, make_float2(a0.w, b0.w));
+    }
+  } else {
+    for (; s < e; ++s) v = compose(v, make_float2(__ldg(a + s), __ldg(b + s)));
+  }
+  return v;
+}
+
+// ranks 0..31 combined in rank order: at mask m the lower rank of each pair
+// comes first; both partners compute the same pair, so every lane ends with
+// the composition of all 32 ranges
+__device__ __forceinline__ float2 lanes_in_order(float2 v, int lane) {
+#pragma unroll
+  for (int m = 1; m < 32; m <<= 1) {
+    const float2 o = make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+    v = (lane & m) ? compose(o, v) : compose(v, o);
+  }
+  return v;
+}
+
+template <int V>
+__global__ void __launch_bounds__(kOrdThreads) ordered_warp_kernel(OrdArgs g) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (kOrdThreads / 32);
+  for (int64_t o = static_cast<int64_t>(blockIdx.x) * (kOrdThreads / 32) + (threadIdx.x >> 5); o < g.O; o += warps) {
+    const int64_t base = o * g.R;
+    const int64_t s = std::min<int64_t>(lane * g.chunk, g.R), e = std::min<int64_t>(s + g.chunk, g.R);
+    float2 v = fold_block<V>(g.a + base, g.b + base, s, e, make_float2(1.0f, 0.0f));
+    v = lanes_in_order(v, lane);
+    if (lane == 0) reinterpret_cast<float2*>(g.out)[o] = v;
+  }
+}
+
+template <int V>
+__global__ void __launch_bounds__(1024) ordered_block_kernel(OrdArgs g) {   // W <= 32 warps per team
+  __shared__ float2 wp[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t items = g.O * g.G;
+  for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+    const int64_t o = item / g.G, pg = item - o * g.G;
+    const int64_t lo = pg * g.part_len, hi = std::min<int64_t>(lo + g.part_len, g.R);
+    const int64_t s = std::min<int64_t>(lo + threadIdx.x * g.chunk, hi), e = std::min<int64_t>(s + g.chunk, hi);
+    float2 v = fold_block<V>(g.a + o * g.R, g.b + o * g.R, s, e, make_float2(1.0f, 0.0f));
+    v = lanes_in_order(v, lane);
+    if (lane == 0) wp[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+      float2 w = lane < g.W ? wp[lane] : make_float2(1.0f, 0.0f);   // the identity map pads the ranks
+      w = lanes_in_order(w, lane);
+      if (lane == 0) {
+        float2* outp = reinterpret_cast<float2*>(g.out);
+        if (g.G == 1) {
+          outp[o] = w;
+        } else {
+          g.part[item] = w;
+          __threadfence();   // publish the part before taking the ticket
+          if (atomicAdd(&g.tickets[o], 1) == g.G - 1) {
+            __threadfence();
+            const volatile float2* pp = g.part + o * g.G;
+            float2 r = make_float2(pp[0].x, pp[0].y);
+            for (int64_t q = 1; q < g.G; ++q) r = compose(r, make_float2(pp[q].x, pp[q].y));   // part order
+            outp[o] = r;
+            g.tickets[o] = 0;   // ready for the next run
+          }
+        }
+      }
+    }
+    __syncthreads();   // wp is rewritten by the next item
+  }
+}
+
+template <class K>
+int blocks_for(K kernel, int threads, int sms) {
+  int per = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0);
+  return std::max(1, per) * sms;
+}
+
+}  // namespace
+
+hp_status ordered_prepare(hp_nest* n) {
+  const OrderedPlan& p = n->ord;
+  if (p.G > 1 && p.O > 0) {
+    n->part_bytes = static_cast<size_t>(p.O * p.G) * sizeof(float2);
+    cudaError_t e = cudaMalloc(&n->part, n->part_bytes);
+    if (e != cudaSuccess) return fail(HP_ENOMEM, "cudaMalloc (ordered parts)");
+    if ((e = cudaMalloc(&n->tickets, sizeof(int32_t) * p.O)) != cudaSuccess)
+      return fail(HP_ENOMEM, "cudaMalloc (ordered tickets)");
+    if ((e = cudaMemset(n->tickets, 0, sizeof(int32_t) * p.O)) != cudaSuccess)
+      return fail(HP_ECUDA, std::string("cudaMemset (tickets): ") + cudaGetErrorString(e));
+  }
+  return HP_OK;
+}
+
+hp_status run_ordered(hp_nest* n, const void* const* in_dev, void* out_dev, cudaStream_t st) {
+  const OrderedPlan& p = n->ord;
+  if (p.O == 0) return HP_OK;
+  if (!out_dev) return fail(HP_EINVAL, "out is NULL");
+  if (p.R > 0 && (!in_dev || !in_dev[0] || !in_dev[1])) return fail(HP_EINVAL, "inputs {a, b} expected");
+  OrdArgs g;
+  g.a = p.R > 0 ? static_cast<const float*>(in_dev[0]) : nullptr;
+  g.b = p.R > 0 ? static_cast<const float*>(in_dev[1]) : nullptr;
+  g.out = static_cast<float*>(out_dev);
+  g.part = static_cast<float2*>(n->part);
+  g.tickets = n->tickets;
+  g.O = p.O;
+  g.R = p.R;
+  g.G = p.G;
+  g.part_len = std::max<int64_t>(p.part, 1);
+  g.chunk = p.chunk;
+  g.W = p.W;
+  const bool v4 = p.V == 4 && (reinterpret_cast<uintptr_t>(g.a) % 16 == 0) && (reinterpret_cast<uintptr_t>(g.b) % 16 == 0);
+  if (reinterpret_cast<uintptr_t>(out_dev) % 8 != 0) return fail(HP_EINVAL, "out must be 8-byte aligned (pairs)");
+  const int sms = n->sms;
+  if (p.team == 0) {
+    const int64_t need = ceil_div(p.O, kOrdThreads / 32);
+    if (v4) {
+      const int grid = static_cast<int>(std::min<int64_t>(need, blocks_for(ordered_warp_kernel<4>, kOrdThreads, sms)));
+      ordered_warp_kernel<4><<<grid, kOrdThreads, 0, st>>>(g);
+    } else {
+      const int grid = static_cast<int>(std::min<int64_t>(need, blocks_for(ordered_warp_kernel<1>, kOrdThreads, sms)));
+      ordered_warp_kernel<1><<<grid, kOrdThreads, 0, st>>>(g);
+    }
+  } else {
+    const int threads = 32 * p.W;
+    const int64_t need = p.O * p.G;
+    if (v4) {
+      const int grid = static_cast<int>(std::min<int64_t>(need, blocks_for(ordered_block_kernel<4>, threads, sms)));
+      ordered_block_kernel<4><<<grid, threads, 0, st>>>(g);
+    } else {
+      const int grid = static_cast<int>(std::min<int64_t>(need, blocks_for(ordered_block_kernel<1>, threads, sms)));
+      ordered_block_kernel<1><<<grid, threads, 0, st>>>(g);
+    }
+  }
+  const cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess) return fail(HP_ECUDA, std::string("ordered launch: ") + cudaGetErrorString(e));
+  return HP_OK;
+}
+
+}  // namespace hp

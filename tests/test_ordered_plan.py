@@ -1,0 +1,58 @@
+"""Ordered (non-commutative) reductions on the CPU: the lowering's teams,
+blocks and grid parts, and rejected descriptors (no GPU)."""
+import pytest
+
+from paper_2309_01906_gb300 import binding as hb
+
+
+def plan(ext, r, lm=None):
+    n = hb.Nest(ext, r, "compose", "f32", "load", level_map=lm)
+    d = n.describe()
+    n.close()
+    return d
+
+
+def test_auto_teams():
+    d = plan([1000, 300], 1)
+    assert d["kind"] == "ordered" and d["team"] == "warp" and d["chunk"] == 12 and d["grid_parts"] == 1   # 300/32 -> 4s
+    d = plan([1000, 5000], 1)
+    assert d["team"] == "block" and d["warps"] == 8 and d["grid_parts"] == 1 and d["chunk"] == 20
+    d = plan([4, 1 << 22], 1)
+    assert d["team"] == "block" and d["grid_parts"] > 1 and d["part"] * (d["grid_parts"] - 1) < (1 << 22)
+    assert d["vec"] == 4 and d["chunk"] % 4 == 0
+    assert d["chain"] == d["chunk"] + 5 + 5 + d["grid_parts"] - 1
+
+
+def test_explicit_maps():
+    d = plan([64, 3, 1000], 1, ["grid", ("cta", 4, 0), ("cta", 4, 0)])
+    assert d["team"] == "block" and d["warps"] == 4 and d["chunk"] == -(-3000 // 128)
+    d = plan([64, 3, 1000], 1, ["grid", ("grid", 0, 1), "grid"])
+    assert d["grid_parts"] == 3 and d["part"] == 1000
+    d = plan([8, 100], 1, ["grid", "warp"])
+    assert d["team"] == "warp" and d["chunk"] == 4
+
+
+@pytest.mark.parametrize("kw,frag", [
+    (dict(prec="f32_comp"), "HP_F32"),
+    (dict(body="dot_bcast"), "HP_BODY_LOAD"),
+    (dict(r=2), "red_level"),
+    (dict(lm=["cta", "warp"]), "output levels on GRID"),
+    (dict(lm=["grid", "subwarp"]), "WARP, CTA or GRID"),
+])
+def test_rejected(kw, frag):
+    r = kw.get("r", 1)
+    with pytest.raises(hb.HPError) as e:
+        hb.Nest([8, 100], r, "compose", kw.get("prec", "f32"), kw.get("body", "load"), level_map=kw.get("lm"))
+    assert e.value.status == hb.HP_EINVAL and frag in str(e.value)
+
+
+def test_ordered_nests_are_not_batched_or_tuned():
+    n = hb.Nest([8, 100], 1, "compose", "f32", "load")
+    with pytest.raises(hb.HPError) as e:
+        hb.hp_nest_run_batch([n.handle], [[0x1000, 0x2000]], [0x3000], 0)
+    assert e.value.status == hb.HP_EUNSUPPORTED
+    with pytest.raises(hb.HPError) as e:
+        n.tune([0x1000, 0x2000], 0x3000)
+    assert e.value.status == hb.HP_EUNSUPPORTED
+    assert 0 < n.error_bound() < 1e-5
+    n.close()
