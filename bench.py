@@ -156,10 +156,11 @@ def run_hp(args):
     plan = nests["f32_comp"].describe()
     launches_per_step = 1 + (1 if plan["grid_parts"] > 1 else 0)
 
+    from paper_2309_01906_gb300 import replicas
+
     def barrier():
         torch.cuda.synchronize()
-        if ws > 1:
-            dist.barrier()
+        replicas.barrier()
         torch.cuda.synchronize()
 
     def timed(nest, steps, warmup):
@@ -190,10 +191,7 @@ def run_hp(args):
     clocks = sampler.stop()
     assert nests["f32_comp"].check(sp) == 0
 
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    max_ms = float(t.item())
+    max_ms = replicas.max_over_ranks(total_ms, device="cuda")   # the slowest replica times the job
 
     # end to end through the C ABI with host buffers: H2D of A and w, run, D2H of out
     hA = torch.from_numpy(A.reshape(-1)).pin_memory()
@@ -208,10 +206,7 @@ def run_hp(args):
         ne.run_host([hA.data_ptr(), hw.data_ptr()], hout.data_ptr(), sp)
     barrier()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_s = float(te.item())
+    e2e_s = replicas.max_over_ranks(e2e_s, device="cuda")
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
