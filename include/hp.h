@@ -335,6 +335,71 @@ hp_status hp_serve_counters(const hp_server *s, uint64_t *completed, uint64_t *s
 void hp_serve_destroy(hp_server *s);
 
 /* ---------------------------------------------------------------------- */
+/* Selecting levels by property (Sec. 3.2: a construct states the features it
+ * needs, `sync(...)`, and the runtime picks the hardware level; Sec. 3.3: a
+ * construct reserves, `reserve(...)`, what its nested constructs need).
+ *
+ * Properties of a hardware level (the paper's table of level properties, as
+ * GB300 provides them to this executor):
+ *   BARRIER    a barrier across the level's tasks (cluster.sync, __syncthreads,
+ *              __syncwarp; the grid has none: no kernel here waits for the grid)
+ *   CRITICAL   mutual exclusion among the level's tasks is implementable
+ *   ATOMIC     atomic read-modify-write on memory the tasks share
+ *   SHUFFLE    register exchange among the tasks (Sec. 3.7: warp lanes)
+ *   OVERSUB    more tasks than run at once (time-shared: grid CTAs)
+ *   DYNAMIC    non-static schedules (Sec. 3.5: an atomic work queue)
+ *   LOCKSTEP   the tasks execute in lockstep (vector slots of one thread)
+ *   PROGRESS   forward progress between tasks (independent thread scheduling)
+ *   GLOBALMEM  the global address space is accessible
+ *   LOCALMEM   memory shared by the level's tasks only (DSMEM, shared memory)
+ *   GROUPMEM   memory private to each task (registers, local memory)
+ *   CACHE      a transparent cache at the level (L2, L1)
+ */
+typedef enum hp_prop {
+    HP_PROP_BARRIER = 1u << 0,
+    HP_PROP_CRITICAL = 1u << 1,
+    HP_PROP_ATOMIC = 1u << 2,
+    HP_PROP_SHUFFLE = 1u << 3,
+    HP_PROP_OVERSUB = 1u << 4,
+    HP_PROP_DYNAMIC = 1u << 5,
+    HP_PROP_LOCKSTEP = 1u << 6,
+    HP_PROP_PROGRESS = 1u << 7,
+    HP_PROP_GLOBALMEM = 1u << 8,
+    HP_PROP_LOCALMEM = 1u << 9,
+    HP_PROP_GROUPMEM = 1u << 10,
+    HP_PROP_CACHE = 1u << 11
+} hp_prop;
+
+/* The properties of hardware level hw (GRID, CLUSTER, CTA, WARP, SUBWARP,
+ * LANE, SEQ) and num = how many tasks of it run in parallel within one unit
+ * of the enclosing level (`num(c)`; the grid: CTAs resident on the device at
+ * 256 threads).  No GPU needed (the device's SM count, if a device is present;
+ * else GB300's 152). */
+hp_status hp_level_properties(hp_hw hw, uint32_t *props, int64_t *num);
+
+/* One nest level's requirements: the `sync` set it needs, the `reserve` set
+ * it must leave to its nested levels, and min_num, the fewest parallel tasks
+ * it needs at its level (0: any). */
+typedef struct {
+    uint32_t sync;
+    uint32_t reserve;
+    int64_t min_num;
+} hp_level_req;
+
+/* Pick a level map for a nest of `depth` levels from their requirements:
+ * level l (outermost first) takes the coarsest hardware level at or below the
+ * previous level's that has req[l].sync and at least req[l].min_num tasks,
+ * such that every inner level can still be placed.  With req[l].reserve set,
+ * the level's own hardware level must lack the reserved properties, a strictly
+ * finer one must have them, and the inner levels start strictly below it (the
+ * level uses every level except those it reserves).  A level with no
+ * requirement stays on its enclosing level (collapse) or, outermost, takes GRID.  SUBWARP is chosen,
+ * with the smallest power-of-two width >= min_num, only when min_num < 32 asks
+ * for fewer lanes than a warp with SHUFFLE.  HP_EINVAL (with the level that
+ * could not be placed) when no map satisfies them. */
+hp_status hp_level_select(int depth, const hp_level_req *req, hp_level_map *map_out);
+
+/* ---------------------------------------------------------------------- */
 /* Stencil nests with ghost zones.
  *
  * Sec. 2: stencils can be tiled to any level that has local memory, a region

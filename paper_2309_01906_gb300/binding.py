@@ -41,7 +41,17 @@ EXPORTED = ["hp_nest_create", "hp_nest_run", "hp_nest_run_host", "hp_nest_run_st
             "hp_nest_describe", "hp_nest_check", "hp_nest_destroy", "hp_serve_create", "hp_serve_submit",
             "hp_serve_poll", "hp_serve_stats", "hp_serve_counters", "hp_serve_destroy", "hp_set_option", "hp_get_option",
             "hp_last_error", "hp_version", "hp_stencil_create", "hp_stencil_run", "hp_stencil_describe",
-            "hp_stencil_check", "hp_stencil_destroy"]
+            "hp_stencil_check", "hp_stencil_destroy", "hp_level_properties", "hp_level_select"]
+
+# level properties (Sec. 3.2)
+PROPS = {"barrier": 1 << 0, "critical": 1 << 1, "atomic": 1 << 2, "shuffle": 1 << 3, "oversub": 1 << 4,
+         "dynamic": 1 << 5, "lockstep": 1 << 6, "progress": 1 << 7, "globalmem": 1 << 8, "localmem": 1 << 9,
+         "groupmem": 1 << 10, "cache": 1 << 11}
+HW_NAMES = {v: k for k, v in HW.items()}
+
+
+class hp_level_req(ctypes.Structure):
+    _fields_ = [("sync", ctypes.c_uint32), ("reserve", ctypes.c_uint32), ("min_num", ctypes.c_int64)]
 
 
 class hp_stencil_map(ctypes.Structure):
@@ -129,6 +139,10 @@ def lib() -> ctypes.CDLL:
         L.hp_set_option.argtypes = [ctypes.c_char_p, i64]
         L.hp_get_option.restype = i32
         L.hp_get_option.argtypes = [ctypes.c_char_p, ctypes.POINTER(i64)]
+        L.hp_level_properties.restype = i32
+        L.hp_level_properties.argtypes = [i32, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(i64)]
+        L.hp_level_select.restype = i32
+        L.hp_level_select.argtypes = [i32, ctypes.POINTER(hp_level_req), ctypes.POINTER(hp_level_map)]
         L.hp_stencil_create.restype = i32
         L.hp_stencil_create.argtypes = [i64, i64, i32, ctypes.POINTER(ctypes.c_float), i32,
                                         ctypes.POINTER(hp_stencil_map), ctypes.POINTER(p)]
@@ -319,6 +333,32 @@ def hp_serve_counters(server):
 def hp_serve_destroy(server):
     if server:
         lib().hp_serve_destroy(server)
+
+
+def _props(names):
+    v = 0
+    for n in names or ():
+        v |= PROPS[n]
+    return v
+
+
+def hp_level_properties(hw):
+    """(set of property names, num) of a hardware level ('grid', 'cluster', ...)."""
+    pr, num = ctypes.c_uint32(), ctypes.c_int64()
+    _check(lib().hp_level_properties(HW[hw], ctypes.byref(pr), ctypes.byref(num)), "hp_level_properties")
+    return {k for k, bit in PROPS.items() if pr.value & bit}, num.value
+
+
+def hp_level_select(reqs):
+    """Level map from per-level requirements: a list of dicts with optional
+    keys sync (property names), reserve (property names) and min_num.
+    Returns [(hw name, sub_width, tile), ...]."""
+    n = len(reqs)
+    arr = (hp_level_req * n)(*[hp_level_req(_props(r.get("sync")), _props(r.get("reserve")), r.get("min_num", 0))
+                               for r in reqs])
+    out = (hp_level_map * n)()
+    _check(lib().hp_level_select(n, arr, out), "hp_level_select")
+    return [(HW_NAMES[m.hw], m.sub_width, m.tile) for m in out]
 
 
 def hp_stencil_create(ny, nx, radius, coeffs, steps, section=(0, 0), tile=(0, 0)):

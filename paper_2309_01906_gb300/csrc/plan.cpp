@@ -19,10 +19,13 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <sstream>
 #include <tuple>
+
+#include <cuda_runtime.h>
 
 #include "hp_internal.h"
 
@@ -534,3 +537,126 @@ double error_bound_rect(const NestPlan& p) {
 }
 
 }  // namespace hp
+
+// ---------------------------------------------------------------- level selection by property
+// Sec. 3.2 (sync clause, the table of level properties) and Sec. 3.3 (reserve).
+namespace hp {
+namespace {
+
+struct LevelCaps {
+  hp_hw hw;
+  uint32_t props;
+};
+
+// GB300 as this executor uses it, coarsest first.  GRID: CTAs are time-shared
+// (not all resident), have no barrier and no forward-progress guarantee among
+// each other, reach L2 and global memory, and take work from atomic queues.
+// CLUSTER: co-scheduled CTAs with a hardware barrier and distributed shared
+// memory.  CTA: warps with __syncthreads, shared memory and L1.  WARP: lanes
+// with __syncwarp and shuffles, independent thread scheduling, registers per
+// lane.  LANE: the vector slots of one thread, advancing in lockstep.  SEQ: a
+// thread's sequential loop.
+constexpr uint32_t P(hp_prop p) { return static_cast<uint32_t>(p); }
+const LevelCaps kCaps[] = {
+    {HP_HW_GRID, P(HP_PROP_ATOMIC) | P(HP_PROP_OVERSUB) | P(HP_PROP_DYNAMIC) | P(HP_PROP_GLOBALMEM) | P(HP_PROP_CACHE)},
+    {HP_HW_CLUSTER, P(HP_PROP_BARRIER) | P(HP_PROP_CRITICAL) | P(HP_PROP_ATOMIC) | P(HP_PROP_PROGRESS) |
+                        P(HP_PROP_GLOBALMEM) | P(HP_PROP_LOCALMEM)},
+    {HP_HW_CTA, P(HP_PROP_BARRIER) | P(HP_PROP_CRITICAL) | P(HP_PROP_ATOMIC) | P(HP_PROP_PROGRESS) |
+                    P(HP_PROP_GLOBALMEM) | P(HP_PROP_LOCALMEM) | P(HP_PROP_CACHE)},
+    {HP_HW_WARP, P(HP_PROP_BARRIER) | P(HP_PROP_CRITICAL) | P(HP_PROP_ATOMIC) | P(HP_PROP_SHUFFLE) |
+                     P(HP_PROP_PROGRESS) | P(HP_PROP_GLOBALMEM) | P(HP_PROP_GROUPMEM)},
+    {HP_HW_LANE, P(HP_PROP_LOCKSTEP) | P(HP_PROP_GLOBALMEM) | P(HP_PROP_GROUPMEM)},
+    {HP_HW_SEQ, P(HP_PROP_LOCKSTEP) | P(HP_PROP_GLOBALMEM) | P(HP_PROP_GROUPMEM)},
+};
+constexpr int kNumCaps = sizeof(kCaps) / sizeof(kCaps[0]);
+
+int device_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+      sms > 0)
+    return sms;
+  cudaGetLastError();   // no device: GB300's count
+  return static_cast<int>(kAssumedSMs);
+}
+
+int64_t level_num(hp_hw hw, int sub) {
+  switch (hw) {
+    case HP_HW_GRID: return static_cast<int64_t>(device_sms()) * 8;   // CTAs of 256 threads resident
+    case HP_HW_CLUSTER: return 8;                                      // portable cluster size (16 opt-in)
+    case HP_HW_CTA: return 32;                                         // warps
+    case HP_HW_WARP: return 32;                                        // lanes
+    case HP_HW_SUBWARP: return sub > 0 ? sub : 16;
+    case HP_HW_LANE: return 4;                                         // 128-bit vector slots
+    default: return 1;
+  }
+}
+
+uint32_t level_props(hp_hw hw) {
+  if (hw == HP_HW_SUBWARP) return kCaps[3].props;   // a partition of the warp keeps its properties (Sec. 3.8)
+  for (const LevelCaps& c : kCaps)
+    if (c.hw == hw) return c.props;
+  return 0;
+}
+
+}  // namespace
+}  // namespace hp
+
+using namespace hp;
+
+extern "C" hp_status hp_level_properties(hp_hw hw, uint32_t* props, int64_t* num) {
+  if (!props || !num) return fail(HP_EINVAL, "NULL argument");
+  if (hw < HP_HW_GRID || hw > HP_HW_SEQ) return fail(HP_EINVAL, "hw must be a hardware level (not AUTO)");
+  *props = level_props(hw);
+  *num = level_num(hw, 0);
+  return HP_OK;
+}
+
+extern "C" hp_status hp_level_select(int depth, const hp_level_req* req, hp_level_map* map_out) {
+  if (depth < 1 || depth > HP_MAX_DEPTH) return fail(HP_EINVAL, "depth must be in [1, HP_MAX_DEPTH]");
+  if (!req || !map_out) return fail(HP_EINVAL, "NULL argument");
+  // can the levels from l on be placed at hardware index >= lo?
+  auto fits = [&](int l, int h) {
+    const hp_level_req& r = req[l];
+    if ((kCaps[h].props & r.sync) != r.sync) return false;
+    const bool sub_ok = kCaps[h].hw == HP_HW_WARP && r.min_num > 0 && r.min_num < 32;   // a sub-warp can serve it
+    if (r.min_num > 0 && level_num(kCaps[h].hw, 0) < r.min_num && !sub_ok) return false;
+    if (r.reserve) {
+      // Sec. 3.3: the level uses every hardware level except those with the
+      // reserved properties, which a strictly finer level must still offer
+      if ((kCaps[h].props & r.reserve) == r.reserve) return false;
+      bool left = false;
+      for (int f = h + 1; f < kNumCaps && !left; ++f) left = (kCaps[f].props & r.reserve) == r.reserve;
+      if (!left) return false;
+    }
+    return true;
+  };
+  // inner levels start at the same hardware level (collapse) or, below a level
+  // that reserves parallelism, strictly below it
+  auto next_lo = [&](int l, int h) { return req[l].reserve ? h + 1 : h; };
+  std::function<bool(int, int)> feasible = [&](int l, int lo) -> bool {
+    if (l == depth) return true;
+    for (int h = lo; h < kNumCaps; ++h)
+      if (fits(l, h) && feasible(l + 1, next_lo(l, h))) return true;
+    return false;
+  };
+  int prev = 0;
+  for (int l = 0; l < depth; ++l) {
+    int pick = -1;
+    for (int h = prev; h < kNumCaps && pick < 0; ++h)
+      if (fits(l, h) && feasible(l + 1, next_lo(l, h))) pick = h;
+    if (pick < 0)
+      return fail(HP_EINVAL, "no hardware level has the properties level " + std::to_string(l) +
+                                 " needs (sync, reserve, min_num) below the levels chosen for the enclosing ones");
+    hp_level_map m = {kCaps[pick].hw, 0, 0};
+    const hp_level_req& r = req[l];
+    if (kCaps[pick].hw == HP_HW_WARP && r.min_num > 0 && r.min_num < 32) {
+      int w = 2;
+      while (w < r.min_num) w *= 2;
+      m = {HP_HW_SUBWARP, w, 0};   // Sec. 3.8: a partition of the warp
+    }
+    map_out[l] = m;
+    prev = next_lo(l, pick);
+  }
+  set_error("");
+  return HP_OK;
+}
