@@ -538,6 +538,46 @@ def run_ordered_workload(args):
                       "cpu_baseline": cpu, "l2": "inputs (2 GiB) larger than L2; no flush"}))
 
 
+def run_narrow_workload(args):
+    """Nests on 8- / 16-bit integers with SIMD-in-register sub-lanes: 1 GiB of
+    uniform values (seed 14) as 16384 x 65536 int8 (dot with an int8 vector,
+    seed 15, and sum) and 16384 x 32768 int16 (max).  Inputs > L2."""
+    import torch
+
+    from paper_2309_01906_gb300 import binding as hb
+    g = np.random.Generator(np.random.PCG64(np.random.SeedSequence(14)))
+    O = 16384
+    stream = torch.cuda.Stream()
+    peak, kind = measured_peaks()
+    res = {}
+    cases = [("i8_dot", "i8", "sum", "dot_bcast", 65536), ("i8_sum", "i8", "sum", "load", 65536),
+             ("i16_max", "i16", "max", "load", 32768)]
+    for name, prec, op, body, R in cases:
+        tdt = torch.int8 if prec == "i8" else torch.int16
+        dA = torch.randint(-128 if prec == "i8" else -32768, 128 if prec == "i8" else 32768, (O * R,), dtype=tdt,
+                           device="cuda", generator=torch.Generator("cuda").manual_seed(int(g.integers(1 << 30))))
+        ins = [dA.data_ptr()]
+        if body == "dot_bcast":
+            dw = torch.randint(-128, 128, (R,), dtype=torch.int8, device="cuda",
+                               generator=torch.Generator("cuda").manual_seed(15))
+            ins.append(dw.data_ptr())
+        out = torch.empty(O, dtype=torch.int32, device="cuda")
+        n = hb.Nest([O, R], 1, op, prec, body)
+        ms = _event_time(lambda: n.run(ins, out.data_ptr(), stream.cuda_stream), args.steps, args.warmup, stream)
+        plan = n.describe()
+        n.close()
+        nbytes = dA.numel() * dA.element_size() + 4 * O
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        res[name] = {"ms": ms, "iterations_per_s": O * R / (ms * 1e-3), "plan": {k: plan[k] for k in
+                     ("team", "warps", "grid_parts", "vec", "simd", "kernel")},
+                     "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                                  "peak_kind": kind, "algorithmic_bytes": nbytes}}
+        del dA
+    print(json.dumps({"workload": "nests on 8- / 16-bit integers, 1 GiB each, SIMD-in-register sub-lanes",
+                      "metric": "nest iterations/s", "steps": args.steps, "warmup": args.warmup, "results": res,
+                      "data": "synthetic (seeded on the device)", "l2": "inputs (1 GiB) larger than L2; no flush"}))
+
+
 def make_uneven_batch(n_nests, seed=9, tune=False, stream=None):
     """The batched workload: n_nests shapes drawn as in synth.uneven_shapes, their
     inputs packed into two device buffers (FP32 for sums, int32 for max), 16-byte
@@ -749,7 +789,7 @@ def main():
     ap.add_argument("--profile-b", type=int, default=0,
                     help="profiler case: run only the headline nest with this outer extent b")
     ap.add_argument("--prec", default="f32_comp", choices=["f32_comp", "f32"])
-    ap.add_argument("--workload", default="nest4", choices=["nest4", "csr", "gemv", "batch", "serve", "stencil", "ordered"],
+    ap.add_argument("--workload", default="nest4", choices=["nest4", "csr", "gemv", "batch", "serve", "stencil", "ordered", "narrow"],
                     help="nest4: the headline line; csr / gemv: measurement of the other workloads")
     ap.add_argument("--csr-rows", type=int, default=1 << 22)
     ap.add_argument("--stencil-n", type=int, default=16384, help="stencil: array side")
@@ -773,6 +813,8 @@ def main():
         run_profile_case(args)
     elif args.workload == "csr":
         run_csr_workload(args)
+    elif args.workload == "narrow":
+        run_narrow_workload(args)
     elif args.workload == "ordered":
         run_ordered_workload(args)
     elif args.workload == "stencil":

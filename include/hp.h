@@ -116,8 +116,27 @@ typedef enum hp_prec {
     HP_F32 = 0,
     HP_F32_COMP = 1,
     HP_I32 = 2,
-    HP_I64 = 3
+    HP_I64 = 3,
+    HP_I8 = 4,    /* int8 inputs, SIMD-in-register sub-lanes (below) */
+    HP_I16 = 5    /* int16 inputs, SIMD-in-register sub-lanes (below) */
 } hp_prec;
+
+/*
+ * HP_I8 / HP_I16 (App. A: CUDA's SIMD intrinsics treat a 32-bit register as 2
+ * x 16-bit or 4 x 8-bit lanes; Sec. 3.8: a level below the lanes).  Rectangular
+ * nests, body LOAD (SUM, MAX, MIN) or DOT_BCAST (HP_I8 only, SUM: int8 x int8
+ * products), in_dev arrays of int8_t / int16_t.  Each thread's 128-bit loads
+ * hold 16 (8) elements, 4 sub-lanes (2) in each 32-bit register: sums and
+ * dot products accumulate into int32 with __dp4a / __dp2a_lo (exact modulo
+ * 2^32), MAX / MIN keep packed running registers (__vmaxs4 / __vmins4,
+ * __vmaxs2 / __vmins2) folded over their sub-lanes at the end.  Outputs int32_t
+ * per output: the sum modulo 2^32, or the max / min value; an empty reduction
+ * gives 0 (SUM) or the type's minimum (MAX) / maximum (MIN).  Level map:
+ * outputs on GRID, the reduced levels on WARP, CTA (sub_width warps) or GRID
+ * (tile > 0: parts combined after a ticket), or AUTO.  Rows whose length or
+ * base is not 16-byte aligned take per-element loads (same results).  Not
+ * batched, served, tuned or run from host buffers.
+ */
 
 /*
  * Bodies (flat = row-major index over all levels, rflat = row-major index over

@@ -55,6 +55,9 @@ hp_status ensure_device(hp_nest* n) {
   } else if (n->kind == NEST_ORDERED) {
     hp_status st = ordered_prepare(n);
     if (st != HP_OK) return st;
+  } else if (n->kind == NEST_NARROW) {
+    hp_status st = narrow_prepare(n);
+    if (st != HP_OK) return st;
   } else {
     hp_status st = csr_prepare(n);
     if (st != HP_OK) return st;
@@ -100,6 +103,7 @@ hp_status run_rect_with(hp_nest* n, const void* const* in_dev, void* out_dev, vo
 
 double error_bound(const hp_nest* n) {
   if (n->kind == NEST_RECT) return error_bound_rect(n->plan);
+  if (n->kind == NEST_NARROW) return 0.0;   // integers: exact
   if (n->kind == NEST_ORDERED) {
     // gamma_{2k}: every iteration passes through at most k folds or combines, each
     // rounding one product and one fused multiply-add
@@ -129,6 +133,7 @@ hp_status tune_release_device(hp_nest* n) {
 size_t out_bytes(const hp_nest* n) {
   if (n->kind == NEST_RECT) return static_cast<size_t>(n->plan.rp.O) * n->plan.out_elem_bytes;
   if (n->kind == NEST_ORDERED) return static_cast<size_t>(n->ord.O) * 2 * sizeof(float);
+  if (n->kind == NEST_NARROW) return static_cast<size_t>(n->nar.O) * sizeof(int32_t);
   return csr_out_bytes(n);
 }
 
@@ -177,7 +182,10 @@ hp_status hp_nest_create(int depth, const int64_t* extents, const int64_t* csr_o
   if (!n) return fail(HP_ENOMEM, "host allocation failed");
   std::string why;
   hp_status st;
-  if (op == HP_RED_AFFINE_COMPOSE) {
+  if (prec == HP_I8 || prec == HP_I16) {
+    n->kind = NEST_NARROW;
+    st = plan_narrow(depth, extents, map, op, red_level, prec, body, &n->nar, &why);
+  } else if (op == HP_RED_AFFINE_COMPOSE) {
     n->kind = NEST_ORDERED;
     st = plan_ordered(depth, extents, map, op, red_level, prec, body, &n->ord, &why);
   } else if (csr_offsets != nullptr || body == HP_BODY_CSR_GATHER || op == HP_RED_HIST_COUNT) {
@@ -204,6 +212,7 @@ hp_status hp_nest_run(hp_nest* n, const void* const* in_dev, void* out_dev, void
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (n->kind == NEST_RECT) return run_rect(n, in_dev, out_dev, s);
   if (n->kind == NEST_ORDERED) return run_ordered(n, in_dev, out_dev, s);
+  if (n->kind == NEST_NARROW) return run_narrow(n, in_dev, out_dev, s);
   return run_csr(n, in_dev, out_dev, s);
 }
 
@@ -264,6 +273,7 @@ hp_status hp_nest_describe(const hp_nest* n, char* buf, size_t len) {
   if (!n || !buf || len == 0) return fail(HP_EINVAL, "NULL argument");
   const std::string s = n->kind == NEST_RECT      ? describe_plan(n->plan)
                         : n->kind == NEST_ORDERED ? describe_ordered(n->ord)
+                        : n->kind == NEST_NARROW  ? describe_narrow(n->nar)
                                                   : describe_csr(n->csr);
   const size_t k = s.size() < len - 1 ? s.size() : len - 1;
   std::memcpy(buf, s.data(), k);

@@ -8,7 +8,7 @@
 #include "hp_internal.h"
 
 namespace hp {
-enum NestKind : int { NEST_RECT = 0, NEST_CSR = 1, NEST_ORDERED = 2 };
+enum NestKind : int { NEST_RECT = 0, NEST_CSR = 1, NEST_ORDERED = 2, NEST_NARROW = 3 };
 struct CsrState;
 }  // namespace hp
 
@@ -17,6 +17,7 @@ struct hp_nest {
   hp::NestPlan plan;          // rectangular nests
   hp::CsrPlan csr;            // CSR nests
   hp::OrderedPlan ord;        // nests with an ordered (non-commutative) reduction
+  hp::NarrowPlan nar;         // nests on 8- / 16-bit integers
   int32_t* tickets = nullptr; // per output, ordered nests split over grid parts
   hp::LaunchCfg cfg;
   int device = -1;            // device of the first run; -1 before it
@@ -57,4 +58,11 @@ hp_status plan_ordered(int depth, const int64_t* extents, const hp_level_map* ma
 std::string describe_ordered(const OrderedPlan& p);
 hp_status ordered_prepare(hp_nest* n);
 hp_status run_ordered(hp_nest* n, const void* const* in_dev, void* out_dev, cudaStream_t st);
+
+// nests on 8- / 16-bit integers (narrow.cu)
+hp_status plan_narrow(int depth, const int64_t* extents, const hp_level_map* map, hp_red_op op, int red_level,
+                      hp_prec prec, hp_body body, NarrowPlan* out, std::string* why);
+std::string describe_narrow(const NarrowPlan& p);
+hp_status narrow_prepare(hp_nest* n);
+hp_status run_narrow(hp_nest* n, const void* const* in_dev, void* out_dev, cudaStream_t st);
 }  // namespace hp

@@ -117,6 +117,25 @@ struct OrderedPlan {
   int32_t k = 0;              // longest chain of folds and combines of one iteration
 };
 
+// Plan of a nest on 8- or 16-bit integers (SIMD sub-lanes in 32-bit
+// registers): outputs over the grid, each output's reduced range [0, R)
+// (contiguous) cut into G parts, a part folded by a team of `threads` threads
+// taking 16-byte pieces cyclically (integer results do not depend on the order).
+struct NarrowPlan {
+  int depth = 0, red_level = 0;
+  int64_t ext[HP_MAX_DEPTH] = {0};
+  hp_level_map map[HP_MAX_DEPTH] = {};
+  bool auto_map = false;
+  hp_red_op op = HP_RED_SUM;
+  hp_prec prec = HP_I8;
+  hp_body body = HP_BODY_LOAD;
+  int32_t esize = 1;          // bytes per element
+  int64_t O = 0, R = 0;
+  int32_t team = 0;           // 0: a warp per output; 1: a CTA of W warps per part
+  int32_t W = 8;
+  int64_t G = 1, part = 0;
+};
+
 // A tuned binding for a shape class (all reduced levels collapsed onto one
 // hardware level, outputs over the grid).
 struct TuneChoice {
