@@ -540,18 +540,22 @@ def run_ordered_workload(args):
 
 def run_narrow_workload(args):
     """Nests on 8- / 16-bit integers with SIMD-in-register sub-lanes: 1 GiB of
-    uniform values (seed 14) as 16384 x 65536 int8 (dot with an int8 vector,
-    seed 15, and sum) and 16384 x 32768 int16 (max).  Inputs > L2."""
+    uniform values (seed 14) as 16384 (--narrow-rows) x 65536 int8 (dot with an
+    int8 vector, seed 15; sum; max) and 16384 x 32768 int16 (sum; max).
+    Inputs > L2."""
     import torch
 
     from paper_2309_01906_gb300 import binding as hb
     g = np.random.Generator(np.random.PCG64(np.random.SeedSequence(14)))
-    O = 16384
+    O = args.narrow_rows
     stream = torch.cuda.Stream()
     peak, kind = measured_peaks()
     res = {}
     cases = [("i8_dot", "i8", "sum", "dot_bcast", 65536), ("i8_sum", "i8", "sum", "load", 65536),
+             ("i8_max", "i8", "max", "load", 65536), ("i16_sum", "i16", "sum", "load", 32768),
              ("i16_max", "i16", "max", "load", 32768)]
+    if args.narrow_cases:
+        cases = [c for c in cases if c[0] in args.narrow_cases.split(",")]
     for name, prec, op, body, R in cases:
         tdt = torch.int8 if prec == "i8" else torch.int16
         dA = torch.randint(-128 if prec == "i8" else -32768, 128 if prec == "i8" else 32768, (O * R,), dtype=tdt,
@@ -573,9 +577,9 @@ def run_narrow_workload(args):
                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                                   "peak_kind": kind, "algorithmic_bytes": nbytes}}
         del dA
-    print(json.dumps({"workload": "nests on 8- / 16-bit integers, 1 GiB each, SIMD-in-register sub-lanes",
+    print(json.dumps({"workload": f"nests on 8- / 16-bit integers, {O} x 64 KiB each, SIMD-in-register sub-lanes",
                       "metric": "nest iterations/s", "steps": args.steps, "warmup": args.warmup, "results": res,
-                      "data": "synthetic (seeded on the device)", "l2": "inputs (1 GiB) larger than L2; no flush"}))
+                      "data": "synthetic (seeded on the device)", "l2": "inputs (64 KiB per row) larger than L2 from 2048 rows on; no flush"}))
 
 
 def make_uneven_batch(n_nests, seed=9, tune=False, stream=None):
@@ -795,6 +799,8 @@ def main():
     ap.add_argument("--stencil-n", type=int, default=16384, help="stencil: array side")
     ap.add_argument("--ordered-rows", type=int, default=64, help="ordered: rows (outputs)")
     ap.add_argument("--ordered-len", type=int, default=1 << 22, help="ordered: maps per row")
+    ap.add_argument("--narrow-rows", type=int, default=16384, help="narrow: rows (outputs) of 64 KiB")
+    ap.add_argument("--narrow-cases", default="", help="narrow: comma list of cases to keep (e.g. i8_dot,i16_sum)")
     ap.add_argument("--stencil-steps", default="1,4", help="stencil: steps per launch to time (comma list)")
     ap.add_argument("--batch-nests", type=int, default=10000)
     ap.add_argument("--batch-breakdown", action="store_true", help="batch: also time each plan class alone")

@@ -165,10 +165,12 @@ struct NarrowOp {
     if constexpr (OP == 0) {
       if constexpr (kI8) acc = __dp4a(static_cast<int>(x), dot ? static_cast<int>(wv) : 0x01010101, acc);
       else acc = __dp2a_lo(static_cast<int>(x), 0x0101, acc);
-    } else if constexpr (OP == 1) {
-      pk = kI8 ? __vmaxs4(pk, x) : __vmaxs2(pk, x);
+    } else if constexpr (kI8) {
+      pk = OP == 1 ? __vmaxs4(pk, x) : __vmins4(pk, x);
+    } else if constexpr (OP == 1) {   // packed 16-bit max / min are native instructions from sm_90 on
+      asm("max.s16x2 %0, %1, %2;" : "=r"(pk) : "r"(pk), "r"(x));
     } else {
-      pk = kI8 ? __vmins4(pk, x) : __vmins2(pk, x);
+      asm("min.s16x2 %0, %1, %2;" : "=r"(pk) : "r"(pk), "r"(x));
     }
   }
   __device__ static __forceinline__ int32_t unpack(uint32_t pk) {   // fold the sub-lanes of a packed register
@@ -202,16 +204,16 @@ __device__ __forceinline__ int32_t fold_range(const E* __restrict__ a, const E* 
   uint32_t pk = Op::packed_ident();
   if constexpr (VEC) {
     constexpr int64_t kP = 16 / sizeof(E);   // elements per 128-bit piece
-    const uint4* av = reinterpret_cast<const uint4*>(a);
-    const uint4* wv = reinterpret_cast<const uint4*>(w);
-    int64_t p = lo / kP + t;
-    const int64_t pe = hi / kP;
-    for (; p + 3 * T < pe; p += 4 * T) {   // four pieces in flight
+    const int64_t first = lo / kP + t, pe = hi / kP;
+    const uint4* ap = reinterpret_cast<const uint4*>(a) + first;
+    const uint4* wq = reinterpret_cast<const uint4*>(w) + first;
+    int64_t n = first < pe ? (pe - first + T - 1) / T : 0;   // pieces of this thread
+    for (; n >= 4; n -= 4, ap += 4 * T, wq += 4 * T) {       // four pieces in flight
       uint4 q[4], r[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        q[u] = __ldcs(av + p + u * T);
-        if constexpr (DOT) r[u] = __ldg(wv + p + u * T);
+        q[u] = __ldcs(ap + u * T);
+        if constexpr (DOT) r[u] = __ldg(wq + u * T);
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -221,10 +223,10 @@ __device__ __forceinline__ int32_t fold_range(const E* __restrict__ a, const E* 
         Op::fold_word(q[u].w, DOT ? r[u].w : 0u, acc, pk, DOT);
       }
     }
-    for (; p < pe; p += T) {
-      const uint4 q = __ldcs(av + p);
+    for (; n > 0; --n, ap += T, wq += T) {
+      const uint4 q = __ldcs(ap);
       uint4 r = make_uint4(0u, 0u, 0u, 0u);
-      if constexpr (DOT) r = __ldg(wv + p);
+      if constexpr (DOT) r = __ldg(wq);
       Op::fold_word(q.x, r.x, acc, pk, DOT);
       Op::fold_word(q.y, r.y, acc, pk, DOT);
       Op::fold_word(q.z, r.z, acc, pk, DOT);
@@ -245,8 +247,14 @@ __device__ __forceinline__ int32_t fold_range(const E* __restrict__ a, const E* 
   return acc;
 }
 
+// Teams of up to 256 threads are compiled for 8 resident CTAs per SM (32
+// registers): a streaming fold needs the bytes in flight of 2048 threads to
+// keep HBM busy.  Larger CTA teams (sub_width up to 32 warps) take a 1024-thread
+// variant.
+constexpr int kNarMinBlocks = 8;
+
 template <class E, int OP, bool DOT, bool VEC>
-__global__ void __launch_bounds__(kNarThreads) narrow_warp_kernel(NarArgs g) {
+__global__ void __launch_bounds__(kNarThreads, kNarMinBlocks) narrow_warp_kernel(NarArgs g) {
   using Op = NarrowOp<E, OP>;
   const int lane = threadIdx.x & 31;
   const int64_t warps = static_cast<int64_t>(gridDim.x) * (kNarThreads / 32);
@@ -259,8 +267,8 @@ __global__ void __launch_bounds__(kNarThreads) narrow_warp_kernel(NarArgs g) {
   }
 }
 
-template <class E, int OP, bool DOT, bool VEC>
-__global__ void __launch_bounds__(1024) narrow_block_kernel(NarArgs g) {
+template <class E, int OP, bool DOT, bool VEC, int MAXT>
+__global__ void __launch_bounds__(MAXT, MAXT == kNarThreads ? kNarMinBlocks : 1) narrow_block_kernel(NarArgs g) {
   using Op = NarrowOp<E, OP>;
   __shared__ int32_t wp[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -311,9 +319,15 @@ cudaError_t launch_narrow(const NarrowPlan& p, const NarArgs& g, int sms, cudaSt
     narrow_warp_kernel<E, OP, DOT, VEC><<<grid, kNarThreads, 0, st>>>(g);
   } else {
     const int threads = 32 * p.W;
-    const int grid = static_cast<int>(
-        std::min<int64_t>(p.O * p.G, nar_blocks(narrow_block_kernel<E, OP, DOT, VEC>, threads, sms)));
-    narrow_block_kernel<E, OP, DOT, VEC><<<grid, threads, 0, st>>>(g);
+    if (threads <= kNarThreads) {
+      auto k = narrow_block_kernel<E, OP, DOT, VEC, kNarThreads>;
+      const int grid = static_cast<int>(std::min<int64_t>(p.O * p.G, nar_blocks(k, threads, sms)));
+      k<<<grid, threads, 0, st>>>(g);
+    } else {
+      auto k = narrow_block_kernel<E, OP, DOT, VEC, 1024>;
+      const int grid = static_cast<int>(std::min<int64_t>(p.O * p.G, nar_blocks(k, threads, sms)));
+      k<<<grid, threads, 0, st>>>(g);
+    }
   }
   return cudaPeekAtLastError();
 }
