@@ -556,6 +556,7 @@ def run_narrow_workload(args):
              ("i16_max", "i16", "max", "load", 32768)]
     if args.narrow_cases:
         cases = [c for c in cases if c[0] in args.narrow_cases.split(",")]
+    cpu = None
     for name, prec, op, body, R in cases:
         tdt = torch.int8 if prec == "i8" else torch.int16
         dA = torch.randint(-128 if prec == "i8" else -32768, 128 if prec == "i8" else 32768, (O * R,), dtype=tdt,
@@ -572,6 +573,20 @@ def run_narrow_workload(args):
         n.close()
         nbytes = dA.numel() * dA.element_size() + 4 * O
         gbs = nbytes / (ms * 1e-3) / 1e9
+        if name == "i8_dot" and not args.no_cpu_baseline:
+            import oracle
+            rows, dt = 1, 0.0
+            Ah = dA[: 1024 * R].cpu().numpy().astype(np.int32)
+            wh = dw.cpu().numpy().astype(np.int32)
+            while rows <= 1024:   # grow the sample until it takes about 2 s
+                t0 = time.perf_counter()
+                oracle.rect([rows, R], 1, "sum", "i32", "dot_bcast", A=Ah[: rows * R], w=wh)
+                dt = time.perf_counter() - t0
+                if dt > 2.0 or rows == 1024:
+                    break
+                rows *= 2
+            cpu = {"value": rows * R / dt, "unit": "iterations/s", "cores": 1, "kind": "oracle",
+                   "sample": f"i8_dot: {rows} rows of {R} (int32 definition on the widened inputs)"}
         res[name] = {"ms": ms, "iterations_per_s": O * R / (ms * 1e-3), "plan": {k: plan[k] for k in
                      ("team", "warps", "grid_parts", "vec", "simd", "kernel")},
                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
@@ -579,7 +594,7 @@ def run_narrow_workload(args):
         del dA
     print(json.dumps({"workload": f"nests on 8- / 16-bit integers, {O} x 64 KiB each, SIMD-in-register sub-lanes",
                       "metric": "nest iterations/s", "steps": args.steps, "warmup": args.warmup, "results": res,
-                      "data": "synthetic (seeded on the device)", "l2": "inputs (64 KiB per row) larger than L2 from 2048 rows on; no flush"}))
+                      "cpu_baseline": cpu, "data": "synthetic (seeded on the device)", "l2": "inputs (64 KiB per row) larger than L2 from 2048 rows on; no flush"}))
 
 
 def make_uneven_batch(n_nests, seed=9, tune=False, stream=None):
