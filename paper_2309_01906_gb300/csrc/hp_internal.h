@@ -112,8 +112,8 @@ struct OrderedPlan {
   int32_t team = 0;           // 0: a warp per output; 1: a CTA of W warps per part
   int32_t W = 8;              // warps per CTA team
   int64_t G = 1, part = 0;    // grid parts per output, iterations per part
-  int64_t chunk = 0;          // iterations per thread (a multiple of 4 when V == 4)
-  int32_t V = 1;              // 4: 128-bit loads (R and part multiples of 4)
+  int64_t chunk = 0;          // iterations per thread (a multiple of V)
+  int32_t V = 1;              // 8: 256-bit loads (R and part multiples of 8); 4: 128-bit loads (multiples of 4)
   int32_t k = 0;              // longest chain of folds and combines of one iteration
 };
 

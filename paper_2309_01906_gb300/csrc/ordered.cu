@@ -101,8 +101,10 @@ hp_status plan_ordered(int depth, const int64_t* extents, const hp_level_map* ma
         // about 8 CTA teams per SM over all parts (2 waves of 4 resident CTAs)
         const int64_t want = std::max<int64_t>(1, ceil_div(8 * 152, std::max<int64_t>(O, 1)));
         part = std::max<int64_t>(16384, ceil_div(R, want));
-        // whole iterations of the first reduced level, and 4-aligned parts (128-bit loads) when R allows
-        const int64_t step = (R % 4 == 0) ? inner * 4 / std::__gcd<int64_t>(inner, 4) : inner;
+        // whole iterations of the first reduced level, and 8- or 4-aligned parts (256- / 128-bit
+        // loads) when R allows
+        const int64_t al = R % 8 == 0 ? 8 : (R % 4 == 0 ? 4 : 1);
+        const int64_t step = inner * al / std::__gcd<int64_t>(inner, al);
         part = ceil_div(part, step) * step;
       }
       p.part = std::max<int64_t>(1, part);
@@ -117,9 +119,9 @@ hp_status plan_ordered(int depth, const int64_t* extents, const hp_level_map* ma
     p.map[l] = {l < red_level ? HP_HW_GRID : red_hw, l >= red_level && red_hw == HP_HW_CTA ? p.W : 0,
                 l == red_level && red_hw == HP_HW_GRID ? p.part / inner : 0};
   const int64_t threads = p.team == 0 ? 32 : 32 * static_cast<int64_t>(p.W);
-  p.V = (R % 4 == 0 && p.part % 4 == 0) ? 4 : 1;
+  p.V = (R % 8 == 0 && p.part % 8 == 0) ? 8 : ((R % 4 == 0 && p.part % 4 == 0) ? 4 : 1);
   p.chunk = std::max<int64_t>(1, ceil_div(std::max<int64_t>(p.part, 1), threads));
-  if (p.V == 4) p.chunk = ceil_div(p.chunk, 4) * 4;
+  p.chunk = ceil_div(p.chunk, p.V) * p.V;
   // longest chain: the thread's block, 5 lane levels, 5 warp levels (CTA teams), the part fold
   p.k = static_cast<int32_t>(std::min<int64_t>(p.chunk + 5 + (p.team ? 5 : 0) + (p.G - 1), int64_t(1) << 30));
   *out = p;
@@ -161,10 +163,36 @@ __device__ __forceinline__ float2 compose(float2 e, float2 l) {
 }
 
 // fold iterations [s, e) of the maps (a, b) into (A, B), in order
+// one 256-bit read-only load (a whole 32-byte sector; the address is 32-byte aligned)
+__device__ __forceinline__ void ld8(const float* p, float* r) {
+  asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7])
+               : "l"(p));
+}
+
 template <int V>
 __device__ __forceinline__ float2 fold_block(const float* __restrict__ a, const float* __restrict__ b, int64_t s,
                                              int64_t e, float2 v) {
-  if constexpr (V == 4) {
+  if constexpr (V == 8) {
+    // a lane walks its own block, so its loads do not coalesce across the
+    // warp; 256-bit loads fetch whole sectors, each in one request
+    for (; s + 16 <= e; s += 16) {
+      float av[16], bv[16];
+      ld8(a + s, av);
+      ld8(a + s + 8, av + 8);
+      ld8(b + s, bv);
+      ld8(b + s + 8, bv + 8);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v = compose(v, make_float2(av[q], bv[q]));
+    }
+    for (; s < e; s += 8) {
+      float av[8], bv[8];
+      ld8(a + s, av);
+      ld8(b + s, bv);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v = compose(v, make_float2(av[q], bv[q]));
+    }
+  } else if constexpr (V == 4) {
     // four 128-bit loads of each input in flight; L1-cached, because a lane
     // walks its own lines (neighbouring lanes are a block apart) and every
     // line serves 8 of its loads
@@ -300,28 +328,30 @@ hp_status run_ordered(hp_nest* n, const void* const* in_dev, void* out_dev, cuda
   g.part_len = std::max<int64_t>(p.part, 1);
   g.chunk = p.chunk;
   g.W = p.W;
-  const bool v4 = p.V == 4 && (reinterpret_cast<uintptr_t>(g.a) % 16 == 0) && (reinterpret_cast<uintptr_t>(g.b) % 16 == 0);
+  // the widest loads the plan and the input alignment allow (blocks start at multiples of V)
+  const uintptr_t al = reinterpret_cast<uintptr_t>(g.a) | reinterpret_cast<uintptr_t>(g.b);
+  const int v = (p.V == 8 && al % 32 == 0) ? 8 : ((p.V >= 4 && al % 16 == 0) ? 4 : 1);
   if (reinterpret_cast<uintptr_t>(out_dev) % 8 != 0) return fail(HP_EINVAL, "out must be 8-byte aligned (pairs)");
   const int sms = n->sms;
   if (p.team == 0) {
     const int64_t need = ceil_div(p.O, kOrdThreads / 32);
-    if (v4) {
-      const int grid = static_cast<int>(std::min<int64_t>(need, blocks_for(ordered_warp_kernel<4>, kOrdThreads, sms)));
-      ordered_warp_kernel<4><<<grid, kOrdThreads, 0, st>>>(g);
-    } else {
-      const int grid = static_cast<int>(std::min<int64_t>(need, blocks_for(ordered_warp_kernel<1>, kOrdThreads, sms)));
-      ordered_warp_kernel<1><<<grid, kOrdThreads, 0, st>>>(g);
-    }
+    auto go = [&](auto kernel) {
+      const int grid = static_cast<int>(std::min<int64_t>(need, blocks_for(kernel, kOrdThreads, sms)));
+      kernel<<<grid, kOrdThreads, 0, st>>>(g);
+    };
+    if (v == 8) go(ordered_warp_kernel<8>);
+    else if (v == 4) go(ordered_warp_kernel<4>);
+    else go(ordered_warp_kernel<1>);
   } else {
     const int threads = 32 * p.W;
     const int64_t need = p.O * p.G;
-    if (v4) {
-      const int grid = static_cast<int>(std::min<int64_t>(need, blocks_for(ordered_block_kernel<4>, threads, sms)));
-      ordered_block_kernel<4><<<grid, threads, 0, st>>>(g);
-    } else {
-      const int grid = static_cast<int>(std::min<int64_t>(need, blocks_for(ordered_block_kernel<1>, threads, sms)));
-      ordered_block_kernel<1><<<grid, threads, 0, st>>>(g);
-    }
+    auto go = [&](auto kernel) {
+      const int grid = static_cast<int>(std::min<int64_t>(need, blocks_for(kernel, threads, sms)));
+      kernel<<<grid, threads, 0, st>>>(g);
+    };
+    if (v == 8) go(ordered_block_kernel<8>);
+    else if (v == 4) go(ordered_block_kernel<4>);
+    else go(ordered_block_kernel<1>);
   }
   const cudaError_t e = cudaPeekAtLastError();
   if (e != cudaSuccess) return fail(HP_ECUDA, std::string("ordered launch: ") + cudaGetErrorString(e));

@@ -89,11 +89,12 @@ def test_exact_when_the_arithmetic_is_exact(ext, r, lm):
     assert Br != Fraction(got[0, 1]) or Ar != Fraction(got[0, 0]) or R < 3
 
 
-def test_misaligned_inputs_give_the_same_results():
+@pytest.mark.parametrize("offset", [1, 4])   # 4 bytes: scalar loads; 16 bytes: 128-bit loads
+def test_misaligned_inputs_give_the_same_results(offset):
     a, b = _inputs(50, 4000, 3)
-    aligned, _, _ = _run([50, 4000], 1, a, b)
-    shifted, _, _ = _run([50, 4000], 1, a, b, offset=1)   # 4-byte offset: scalar loads
-    assert np.array_equal(aligned, shifted)
+    aligned, d, _ = _run([50, 4000], 1, a, b)   # 32-byte aligned: 256-bit loads
+    shifted, _, _ = _run([50, 4000], 1, a, b, offset=offset)
+    assert d["vec"] == 8 and np.array_equal(aligned, shifted)
 
 
 def test_empty_ranges_give_the_identity_map():

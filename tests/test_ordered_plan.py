@@ -15,11 +15,13 @@ def plan(ext, r, lm=None):
 def test_auto_teams():
     d = plan([1000, 300], 1)
     assert d["kind"] == "ordered" and d["team"] == "warp" and d["chunk"] == 12 and d["grid_parts"] == 1   # 300/32 -> 4s
+    assert d["vec"] == 4                                  # 300 is a multiple of 4, not of 8
     d = plan([1000, 5000], 1)
-    assert d["team"] == "block" and d["warps"] == 8 and d["grid_parts"] == 1 and d["chunk"] == 20
+    assert d["team"] == "block" and d["warps"] == 8 and d["grid_parts"] == 1 and d["chunk"] == 24   # 5000/256 -> 8s
+    assert d["vec"] == 8
     d = plan([4, 1 << 22], 1)
     assert d["team"] == "block" and d["grid_parts"] > 1 and d["part"] * (d["grid_parts"] - 1) < (1 << 22)
-    assert d["vec"] == 4 and d["chunk"] % 4 == 0
+    assert d["vec"] == 8 and d["chunk"] % 8 == 0 and d["part"] % 8 == 0
     assert d["chain"] == d["chunk"] + 5 + 5 + d["grid_parts"] - 1
 
 
@@ -30,6 +32,8 @@ def test_explicit_maps():
     assert d["grid_parts"] == 3 and d["part"] == 1000
     d = plan([8, 100], 1, ["grid", "warp"])
     assert d["team"] == "warp" and d["chunk"] == 4
+    d = plan([8, 102], 1, ["grid", "warp"])
+    assert d["vec"] == 1 and d["chunk"] == 4
 
 
 @pytest.mark.parametrize("kw,frag", [
