@@ -412,11 +412,34 @@ typedef struct {
  * the level's own hardware level must lack the reserved properties, a strictly
  * finer one must have them, and the inner levels start strictly below it (the
  * level uses every level except those it reserves).  A level with no
- * requirement stays on its enclosing level (collapse) or, outermost, takes GRID.  SUBWARP is chosen,
- * with the smallest power-of-two width >= min_num, only when min_num < 32 asks
- * for fewer lanes than a warp with SHUFFLE.  HP_EINVAL (with the level that
- * could not be placed) when no map satisfies them. */
+ * requirement stays on its enclosing level (collapse) or, outermost, takes GRID.
+ * At the warp's level, 0 < min_num < 32 asks for a sub-warp partition (Sec.
+ * 3.8): the narrowest power-of-two width >= min_num whose inner levels can
+ * still be placed (up to the whole warp); an inner level that collapses onto
+ * a sub-warp partition keeps its width.  HP_EINVAL (with the level that could
+ * not be placed) when no map satisfies them: selection succeeds exactly when
+ * some map passes hp_level_check. */
 hp_status hp_level_select(int depth, const hp_level_req *req, hp_level_map *map_out);
+
+/* Does `map` (depth entries, no AUTO) meet the requirements `req`, under the
+ * rules of hp_level_select?  Each level must be at or below its enclosing
+ * level's hardware level (strictly below one that reserves), have the sync
+ * properties, at least min_num tasks (the team size the map gives a CTA,
+ * sub-warp or vector level, else the level's capacity) and, with a reserve
+ * set, lack those properties while a finer level has them.  HP_OK, or
+ * HP_EINVAL with the first level that fails in hp_last_error.  Host only. */
+hp_status hp_level_check(int depth, const hp_level_req *req, const hp_level_map *map);
+
+/* hp_nest_tune with requirements as its constraint language (Sec. 3.2: a
+ * construct states what it needs and the implementation picks the level):
+ * req[depth] as for hp_level_select.  Only candidate maps that meet them are
+ * timed (hp_level_check), with the map hp_level_select derives from them
+ * first; flags as for hp_nest_tune.  The winner is cached for the shape class
+ * under this set of requirements only: nests created later with map == NULL
+ * never take it.  HP_EINVAL when no candidate meets the requirements (a nest
+ * whose levels are all outputs: when its map does not). */
+hp_status hp_nest_tune_req(hp_nest *n, const hp_level_req *req, const void *const *in_dev, void *out_dev,
+                           void *stream, int32_t flags);
 
 /* ---------------------------------------------------------------------- */
 /* Stencil nests with ghost zones.

@@ -37,11 +37,12 @@ BODIES = {"load": HP_BODY_LOAD, "dot_bcast": HP_BODY_DOT_BCAST, "csr_gather": HP
 
 # every entry point include/hp.h declares
 EXPORTED = ["hp_nest_create", "hp_nest_run", "hp_nest_run_host", "hp_nest_run_static", "hp_nest_run_batch",
-            "hp_nest_tune", "hp_nest_error_bound",
+            "hp_nest_tune", "hp_nest_tune_req", "hp_nest_error_bound",
             "hp_nest_describe", "hp_nest_check", "hp_nest_destroy", "hp_serve_create", "hp_serve_submit",
             "hp_serve_poll", "hp_serve_stats", "hp_serve_counters", "hp_serve_destroy", "hp_set_option", "hp_get_option",
             "hp_last_error", "hp_version", "hp_stencil_create", "hp_stencil_run", "hp_stencil_describe",
-            "hp_stencil_check", "hp_stencil_destroy", "hp_level_properties", "hp_level_select"]
+            "hp_stencil_check", "hp_stencil_destroy", "hp_level_properties", "hp_level_select",
+            "hp_level_check"]
 
 # level properties (Sec. 3.2)
 PROPS = {"barrier": 1 << 0, "critical": 1 << 1, "atomic": 1 << 2, "shuffle": 1 << 3, "oversub": 1 << 4,
@@ -143,6 +144,10 @@ def lib() -> ctypes.CDLL:
         L.hp_level_properties.argtypes = [i32, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(i64)]
         L.hp_level_select.restype = i32
         L.hp_level_select.argtypes = [i32, ctypes.POINTER(hp_level_req), ctypes.POINTER(hp_level_map)]
+        L.hp_level_check.restype = i32
+        L.hp_level_check.argtypes = [i32, ctypes.POINTER(hp_level_req), ctypes.POINTER(hp_level_map)]
+        L.hp_nest_tune_req.restype = i32
+        L.hp_nest_tune_req.argtypes = [p, ctypes.POINTER(hp_level_req), p, p, p, ctypes.c_int32]
         L.hp_stencil_create.restype = i32
         L.hp_stencil_create.argtypes = [i64, i64, i32, ctypes.POINTER(ctypes.c_float), i32,
                                         ctypes.POINTER(hp_stencil_map), ctypes.POINTER(p)]
@@ -263,12 +268,17 @@ class PreparedRun:
         _check(st, "hp_nest_run")
 
 
-def hp_nest_tune(nest, in_ptrs, out_ptr, stream=0, retime=False, batched=False):
+def hp_nest_tune(nest, in_ptrs, out_ptr, stream=0, retime=False, batched=False, req=None):
     """Time candidate bindings on these buffers, install the fastest (synchronous);
-    batched=True times them in the batched executor (flags bit 1)."""
+    batched=True times them in the batched executor (flags bit 1); req: per-level
+    requirements (as for hp_level_select) that every timed map must meet."""
     flags = (1 if retime else 0) | (2 if batched else 0)
-    st = lib().hp_nest_tune(nest, _ptr_array(in_ptrs), out_ptr or None, stream or None, flags)
-    _check(st, "hp_nest_tune")
+    if req is None:
+        st = lib().hp_nest_tune(nest, _ptr_array(in_ptrs), out_ptr or None, stream or None, flags)
+        _check(st, "hp_nest_tune")
+    else:
+        st = lib().hp_nest_tune_req(nest, _req_array(req), _ptr_array(in_ptrs), out_ptr or None, stream or None, flags)
+        _check(st, "hp_nest_tune_req")
 
 
 def hp_nest_error_bound(nest) -> float:
@@ -349,16 +359,32 @@ def hp_level_properties(hw):
     return {k for k, bit in PROPS.items() if pr.value & bit}, num.value
 
 
+def _req_array(reqs):
+    return (hp_level_req * len(reqs))(*[hp_level_req(_props(r.get("sync")), _props(r.get("reserve")),
+                                                     r.get("min_num", 0)) for r in reqs])
+
+
 def hp_level_select(reqs):
     """Level map from per-level requirements: a list of dicts with optional
     keys sync (property names), reserve (property names) and min_num.
     Returns [(hw name, sub_width, tile), ...]."""
     n = len(reqs)
-    arr = (hp_level_req * n)(*[hp_level_req(_props(r.get("sync")), _props(r.get("reserve")), r.get("min_num", 0))
-                               for r in reqs])
     out = (hp_level_map * n)()
-    _check(lib().hp_level_select(n, arr, out), "hp_level_select")
+    _check(lib().hp_level_select(n, _req_array(reqs), out), "hp_level_select")
     return [(HW_NAMES[m.hw], m.sub_width, m.tile) for m in out]
+
+
+def hp_level_check(reqs, level_map):
+    """True if the level map (as for Nest's level_map) meets the requirements;
+    False with the reason otherwise: returns (ok, message)."""
+    n = len(reqs)
+    mp = level_map if isinstance(level_map, ctypes.Array) else make_map(level_map)
+    st = lib().hp_level_check(n, _req_array(reqs), mp)
+    if st == HP_OK:
+        return True, ""
+    if st != HP_EINVAL:
+        _check(st, "hp_level_check")
+    return False, hp_last_error()
 
 
 def hp_stencil_create(ny, nx, radius, coeffs, steps, section=(0, 0), tile=(0, 0)):
@@ -447,8 +473,8 @@ class Nest:
     def run_host(self, in_ptrs, out_ptr, stream=0):
         hp_nest_run_host(self.handle, in_ptrs, out_ptr, stream)
 
-    def tune(self, in_ptrs, out_ptr, stream=0, retime=False, batched=False):
-        hp_nest_tune(self.handle, in_ptrs, out_ptr, stream, retime, batched)
+    def tune(self, in_ptrs, out_ptr, stream=0, retime=False, batched=False, req=None):
+        hp_nest_tune(self.handle, in_ptrs, out_ptr, stream, retime, batched, req)
 
     def describe(self) -> dict:
         return hp_nest_describe(self.handle)

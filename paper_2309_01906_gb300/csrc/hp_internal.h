@@ -142,15 +142,20 @@ struct TuneChoice {
   int32_t red_hw = HP_HW_AUTO;  // hardware level of the reduced levels (AUTO: the planner's map)
   int32_t sub = 0;              // SUBWARP width, LANE vector slots, or CTA warps
   int64_t split_parts = 0;      // > 0: reduced levels split over this many grid parts
+  int32_t n_map = 0;            // > 0: this explicit map instead (the map chosen from level requirements)
+  hp_level_map map[HP_MAX_DEPTH] = {};
 };
 struct TuneKey {
   int32_t lo, lr, vec, body, prec, op;
+  uint64_t req = 0;             // hash of the level requirements the choice was made under (0: none)
   bool operator<(const TuneKey& o) const;
 };
 TuneKey tune_key(const NestPlan& p);
 bool tune_lookup(const TuneKey& k, TuneChoice* c);
 void tune_store(const TuneKey& k, const TuneChoice& c);
 void tune_apply(const NestPlan& p, const TuneChoice& c, hp_level_map* m);
+// does the map meet the per-level requirements (the rules of hp_level_select)?
+bool map_meets(int depth, const hp_level_req* req, const hp_level_map* map, std::string* why);
 size_t tune_cache_size();
 
 // Validate a rectangular nest and build its plan.  Returns HP_OK or an error

@@ -75,7 +75,7 @@ int32_t ceil_log2(int64_t v) {
 }  // namespace
 
 bool TuneKey::operator<(const TuneKey& o) const {
-  return std::tie(lo, lr, vec, body, prec, op) < std::tie(o.lo, o.lr, o.vec, o.body, o.prec, o.op);
+  return std::tie(lo, lr, vec, body, prec, op, req) < std::tie(o.lo, o.lr, o.vec, o.body, o.prec, o.op, o.req);
 }
 
 // shape class: log2 buckets of outputs and reduced size, whether the reduced
@@ -111,6 +111,10 @@ static void auto_map(const NestPlan& p, hp_level_map* m);
 // outputs over the grid; every reduced level on the chosen hardware level
 // (HP_HW_AUTO: the planner's own map)
 void tune_apply(const NestPlan& p, const TuneChoice& c, hp_level_map* m) {
+  if (c.n_map > 0) {
+    for (int l = 0; l < p.depth; ++l) m[l] = c.map[l];
+    return;
+  }
   if (c.red_hw == HP_HW_AUTO) {
     auto_map(p, m);
     return;
@@ -598,7 +602,58 @@ uint32_t level_props(hp_hw hw) {
   return 0;
 }
 
+// coarse-to-fine position of a hardware level; a sub-warp partition sits
+// between the warp and the vector slots
+int level_rank(int hw) {
+  switch (hw) {
+    case HP_HW_GRID: return 0;
+    case HP_HW_CLUSTER: return 2;
+    case HP_HW_CTA: return 4;
+    case HP_HW_WARP: return 6;
+    case HP_HW_SUBWARP: return 7;
+    case HP_HW_LANE: return 8;
+    case HP_HW_SEQ: return 10;
+    default: return -1;
+  }
+}
+
 }  // namespace
+
+bool map_meets(int depth, const hp_level_req* req, const hp_level_map* map, std::string* why) {
+  for (int l = 0; l < depth; ++l) {
+    const hp_level_req& r = req[l];
+    const int hw = map[l].hw;
+    const int rank = level_rank(hw);
+    auto no = [&](const std::string& m) {
+      *why = "level " + std::to_string(l) + ": " + m;
+      return false;
+    };
+    if (rank < 0) return no("not a hardware level (AUTO maps are checked after planning)");
+    if (l > 0) {
+      const int prev = level_rank(map[l - 1].hw);
+      if (rank < prev) return no("coarser than its enclosing level");
+      if (req[l - 1].reserve && rank == prev) return no("on the level its enclosing level reserves parallelism below");
+      if (hw == HP_HW_SUBWARP && map[l - 1].hw == HP_HW_SUBWARP && map[l].sub_width > map[l - 1].sub_width)
+        return no("a sub-warp partition wider than its enclosing one");
+    }
+    const uint32_t props = level_props(static_cast<hp_hw>(hw));
+    if ((props & r.sync) != r.sync) return no("its hardware level lacks a required sync property");
+    // tasks of the level: the team's size where the map fixes one (CTA warps,
+    // sub-warp width, vector slots), else the level's capacity
+    const int sub = map[l].sub_width;
+    const int64_t num = (sub > 0 && (hw == HP_HW_CTA || hw == HP_HW_SUBWARP || hw == HP_HW_LANE))
+                            ? sub : level_num(static_cast<hp_hw>(hw), 0);
+    if (r.min_num > 0 && num < r.min_num) return no("fewer parallel tasks than min_num");
+    if (r.reserve) {
+      if ((props & r.reserve) == r.reserve) return no("its hardware level has the properties it reserves");
+      bool left = false;
+      for (const LevelCaps& c : kCaps) left = left || (level_rank(c.hw) > rank && (c.props & r.reserve) == r.reserve);
+      if (!left) return no("no finer hardware level has the reserved properties");
+    }
+  }
+  return true;
+}
+
 }  // namespace hp
 
 using namespace hp;
@@ -611,15 +666,25 @@ extern "C" hp_status hp_level_properties(hp_hw hw, uint32_t* props, int64_t* num
   return HP_OK;
 }
 
+extern "C" hp_status hp_level_check(int depth, const hp_level_req* req, const hp_level_map* map) {
+  if (depth < 1 || depth > HP_MAX_DEPTH) return fail(HP_EINVAL, "depth must be in [1, HP_MAX_DEPTH]");
+  if (!req || !map) return fail(HP_EINVAL, "NULL argument");
+  std::string why;
+  if (!map_meets(depth, req, map, &why)) return fail(HP_EINVAL, why);
+  set_error("");
+  return HP_OK;
+}
+
 extern "C" hp_status hp_level_select(int depth, const hp_level_req* req, hp_level_map* map_out) {
   if (depth < 1 || depth > HP_MAX_DEPTH) return fail(HP_EINVAL, "depth must be in [1, HP_MAX_DEPTH]");
   if (!req || !map_out) return fail(HP_EINVAL, "NULL argument");
-  // can the levels from l on be placed at hardware index >= lo?
-  auto fits = [&](int l, int h) {
+  // wcap: the lanes a level at the warp's index may use (32, or the width of
+  // the enclosing sub-warp partition it collapses onto); w: the lanes it takes
+  auto fits = [&](int l, int h, int w) {
     const hp_level_req& r = req[l];
     if ((kCaps[h].props & r.sync) != r.sync) return false;
-    const bool sub_ok = kCaps[h].hw == HP_HW_WARP && r.min_num > 0 && r.min_num < 32;   // a sub-warp can serve it
-    if (r.min_num > 0 && level_num(kCaps[h].hw, 0) < r.min_num && !sub_ok) return false;
+    const int64_t num = kCaps[h].hw == HP_HW_WARP ? w : level_num(kCaps[h].hw, 0);
+    if (r.min_num > 0 && num < r.min_num) return false;
     if (r.reserve) {
       // Sec. 3.3: the level uses every hardware level except those with the
       // reserved properties, which a strictly finer level must still offer
@@ -630,32 +695,54 @@ extern "C" hp_status hp_level_select(int depth, const hp_level_req* req, hp_leve
     }
     return true;
   };
-  // inner levels start at the same hardware level (collapse) or, below a level
-  // that reserves parallelism, strictly below it
+  // the partitions a level may take at index h, in order of preference: at the
+  // warp's index the narrowest power-of-two sub-warp with min_num lanes first
+  // (Sec. 3.8), wider ones up to the whole warp if its inner levels need them,
+  // or only the enclosing partition it collapses onto
+  auto widths = [&](int l, int h, int wcap) {
+    std::vector<int> ws;
+    if (kCaps[h].hw != HP_HW_WARP) {
+      ws.push_back(32);
+    } else if (wcap < 32) {
+      ws.push_back(wcap);
+    } else {
+      const int64_t mn = req[l].min_num;
+      int w = 32;
+      if (mn > 0 && mn < 32) {
+        w = 2;
+        while (w < mn) w *= 2;
+      }
+      for (; w <= 32; w *= 2) ws.push_back(w);
+    }
+    return ws;
+  };
+  // inner levels start at the same hardware level (collapse, keeping a
+  // sub-warp partition) or, below a level that reserves parallelism, strictly
+  // below it
   auto next_lo = [&](int l, int h) { return req[l].reserve ? h + 1 : h; };
-  std::function<bool(int, int)> feasible = [&](int l, int lo) -> bool {
+  auto next_w = [&](int l, int h, int w) { return (req[l].reserve || kCaps[h].hw != HP_HW_WARP) ? 32 : w; };
+  std::function<bool(int, int, int)> feasible = [&](int l, int lo, int wcap) -> bool {
     if (l == depth) return true;
     for (int h = lo; h < kNumCaps; ++h)
-      if (fits(l, h) && feasible(l + 1, next_lo(l, h))) return true;
+      for (int w : widths(l, h, wcap))
+        if (fits(l, h, w) && feasible(l + 1, next_lo(l, h), next_w(l, h, w))) return true;
     return false;
   };
-  int prev = 0;
+  int prev = 0, wcap = 32;
   for (int l = 0; l < depth; ++l) {
-    int pick = -1;
+    int pick = -1, pw = 32;
     for (int h = prev; h < kNumCaps && pick < 0; ++h)
-      if (fits(l, h) && feasible(l + 1, next_lo(l, h))) pick = h;
+      for (int w : widths(l, h, wcap))
+        if (pick < 0 && fits(l, h, w) && feasible(l + 1, next_lo(l, h), next_w(l, h, w))) {
+          pick = h;
+          pw = w;
+        }
     if (pick < 0)
       return fail(HP_EINVAL, "no hardware level has the properties level " + std::to_string(l) +
                                  " needs (sync, reserve, min_num) below the levels chosen for the enclosing ones");
-    hp_level_map m = {kCaps[pick].hw, 0, 0};
-    const hp_level_req& r = req[l];
-    if (kCaps[pick].hw == HP_HW_WARP && r.min_num > 0 && r.min_num < 32) {
-      int w = 2;
-      while (w < r.min_num) w *= 2;
-      m = {HP_HW_SUBWARP, w, 0};   // Sec. 3.8: a partition of the warp
-    }
-    map_out[l] = m;
+    map_out[l] = pw < 32 ? hp_level_map{HP_HW_SUBWARP, pw, 0} : hp_level_map{kCaps[pick].hw, 0, 0};
     prev = next_lo(l, pick);
+    wcap = next_w(l, pick, pw);
   }
   set_error("");
   return HP_OK;

@@ -115,15 +115,54 @@ hp_status time_plan_batched(hp_nest* tmp, const void* const* in_dev, void* out_d
 
 using namespace hp;
 
-extern "C" hp_status hp_nest_tune(hp_nest* n, const void* const* in_dev, void* out_dev, void* stream, int32_t flags) {
+namespace hp {
+namespace {
+
+// FNV-1a over the requirement triples: the cache key of choices made under them
+uint64_t req_hash(int depth, const hp_level_req* req) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](uint64_t v) {
+    for (int i = 0; i < 8; ++i) {
+      h ^= (v >> (8 * i)) & 0xffu;
+      h *= 1099511628211ull;
+    }
+  };
+  mix(static_cast<uint64_t>(depth));
+  for (int l = 0; l < depth; ++l) {
+    mix(req[l].sync);
+    mix(req[l].reserve);
+    mix(static_cast<uint64_t>(req[l].min_num));
+  }
+  return h | 1u;   // never 0 (0 = no requirements)
+}
+
+hp_status tune_impl(hp_nest* n, const hp_level_req* req, const void* const* in_dev, void* out_dev, void* stream,
+                    int32_t flags) {
   if (!n) return fail(HP_EINVAL, "nest is NULL");
   if (n->kind != NEST_RECT) return fail(HP_EUNSUPPORTED, "only rectangular nests are tuned");
   NestPlan& p = n->plan;
-  if (p.red_level == p.depth) return HP_OK;  // nothing is reduced: nothing to bind
+  if (p.red_level == p.depth) {   // nothing is reduced: nothing to bind, only the map to check
+    std::string why;
+    if (req && !map_meets(p.depth, req, p.map, &why)) return fail(HP_EINVAL, "the nest's map: " + why);
+    return HP_OK;
+  }
+  if (req) {   // host check first: unsatisfiable requirements need no device
+    bool any = false;
+    hp_level_map m[HP_MAX_DEPTH];
+    any = hp_level_select(p.depth, req, m) == HP_OK;
+    std::string why;
+    for (const TuneChoice& c : candidates(p, n->sms > 0 ? n->sms : 152, true)) {   // GB300 before the first run
+      if (any) break;
+      tune_apply(p, c, m);
+      any = map_meets(p.depth, req, m, &why);
+    }
+    if (!any) return fail(HP_EINVAL, "no candidate map meets the level requirements (" + why + ")");
+  }
   hp_status s = ensure_device(n);
   if (s != HP_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const TuneKey key = tune_key(p);
+  TuneKey key = tune_key(p);
+  if (req) key.req = req_hash(p.depth, req);
   TuneChoice best;
   const bool reuse = (flags & 1) == 0;
   const bool batched = (flags & 2) != 0;
@@ -134,7 +173,31 @@ extern "C" hp_status hp_nest_tune(hp_nest* n, const void* const* in_dev, void* o
   if (!have) {
     float best_ms = FLT_MAX;
     float auto_ms = -1.0f;
-    const std::vector<TuneChoice> cand = candidates(p, n->sms, batched);
+    std::vector<TuneChoice> cand = candidates(p, n->sms, batched || req);
+    if (req) {
+      // Sec. 3.2: the requirements are the constraint language; only maps that
+      // meet them are timed, and the map chosen from them comes first
+      std::vector<TuneChoice> kept;
+      TuneChoice sel;
+      if (hp_level_select(p.depth, req, sel.map) == HP_OK) {
+        sel.n_map = p.depth;
+        kept.push_back(sel);
+      }
+      for (const TuneChoice& c : cand) {
+        hp_level_map m[HP_MAX_DEPTH];
+        tune_apply(p, c, m);
+        std::string why;
+        if (map_meets(p.depth, req, m, &why)) kept.push_back(c);
+      }
+      if (kept.empty()) {
+        std::string why;
+        hp_level_map m[HP_MAX_DEPTH];
+        tune_apply(p, TuneChoice{}, m);
+        map_meets(p.depth, req, m, &why);
+        return fail(HP_EINVAL, "no candidate map meets the level requirements (" + why + ")");
+      }
+      cand.swap(kept);
+    }
     for (const TuneChoice& c : cand) {
       hp_level_map m[HP_MAX_DEPTH];
       tune_apply(p, c, m);
@@ -156,7 +219,7 @@ extern "C" hp_status hp_nest_tune(hp_nest* n, const void* const* in_dev, void* o
         if (ts == HP_ECUDA) return ts;
         continue;
       }
-      if (c.red_hw == HP_HW_AUTO) auto_ms = ms;
+      if (c.red_hw == HP_HW_AUTO && c.n_map == 0) auto_ms = ms;
       if (ms < best_ms) {
         best_ms = ms;
         best = c;
@@ -165,7 +228,8 @@ extern "C" hp_status hp_nest_tune(hp_nest* n, const void* const* in_dev, void* o
     }
     // batched: keep the planner's map unless another one is clearly faster
     if (batched && auto_ms >= 0.0f && best_ms > 0.97f * auto_ms) best = TuneChoice{};
-    if (!have) return fail(HP_EUNSUPPORTED, "no candidate binding runs for this shape");
+    if (!have) return fail(req ? HP_EINVAL : HP_EUNSUPPORTED, req ? "no map that meets the level requirements runs for this shape"
+                                                                 : "no candidate binding runs for this shape");
     tune_store(key, best);
   }
   // install the winner in this nest (its device scratch is sized per plan)
@@ -189,4 +253,17 @@ extern "C" hp_status hp_nest_tune(hp_nest* n, const void* const* in_dev, void* o
   s = ensure_device(n);
   if (s != HP_OK) return s;
   return run_rect(n, in_dev, out_dev, st);  // the outputs hold the installed plan's result
+}
+
+}  // namespace
+}  // namespace hp
+
+extern "C" hp_status hp_nest_tune(hp_nest* n, const void* const* in_dev, void* out_dev, void* stream, int32_t flags) {
+  return tune_impl(n, nullptr, in_dev, out_dev, stream, flags);
+}
+
+extern "C" hp_status hp_nest_tune_req(hp_nest* n, const hp_level_req* req, const void* const* in_dev, void* out_dev,
+                                      void* stream, int32_t flags) {
+  if (!req) return fail(HP_EINVAL, "req is NULL (use hp_nest_tune)");
+  return tune_impl(n, req, in_dev, out_dev, stream, flags);
 }

@@ -50,3 +50,31 @@ def test_tune_installs_and_caches(ext, r, op, prec, batched):
     assert torch.equal(out, out3)
     n.close()
     n2.close()
+
+
+@pytest.mark.parametrize("ext,req,allowed", [
+    ([2000, 384], [{}, {"sync": ["shuffle"]}], {"warp", "subwarp"}),
+    ([2000, 384], [{}, {"sync": ["barrier", "localmem"]}], {"cta", "cluster"}),
+    ([4000, 64], [{}, {"sync": ["lockstep"]}], {"lane", "seq"}),
+])
+def test_tune_under_level_requirements(ext, req, allowed):
+    # Sec. 3.2 requirements as the tuner's constraint language: only maps that
+    # meet them are timed; the winner is cached under them alone
+    import torch
+    rng = np.random.Generator(np.random.PCG64(17))
+    A = rng.standard_normal(int(np.prod(ext))).astype(np.float32)
+    dA = torch.from_numpy(A).cuda()
+    out = torch.empty(ext[0], dtype=torch.float32, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    n = hb.Nest(ext, 1, "sum", "f32_comp", "load")
+    n.tune([dA.data_ptr()], out.data_ptr(), s, retime=True, req=req)
+    d = n.describe()
+    assert d["tuned"] and d["map"][1]["hw"] in allowed, d["map"]
+    assert hb.hp_level_check(req, [(m["hw"], m["sub_width"], m["tile"]) for m in d["map"]])[0]
+    torch.cuda.synchronize()
+    ref = oracle_rect(ext, 1, "sum", "f32_comp", "load", A=A)
+    assert_close(out.cpu().numpy(), ref, "f32_comp", "sum", n.error_bound(), what=f"tuned under {req}")
+    fresh = hb.Nest(ext, 1, "sum", "f32_comp", "load")   # an automatic nest of the class: not given the choice
+    assert not fresh.describe()["tuned"]
+    fresh.close()
+    n.close()
