@@ -21,6 +21,18 @@ Combining two adjacent ranges, the earlier (A1, B1) and the later (A2, B2):
 evaluates the two sums/products with numpy's cumulative products (a second
 formulation); ``compose_exact`` works in exact rationals; ``abs_bound`` gives
 |A| and sum |b_x| prod_{z > x} |a_z| (the scale of rounding errors).
+
+Two more non-commutative operators of the same kind:
+
+* 2x2 matrix products in iteration order, M = M_{R-1} ... M_1 M_0 (the later
+  matrix on the left), each iteration's matrix stored row-major as 4 values;
+  combining adjacent ranges: (earlier E, later L) -> L E; identity I.  The
+  affine maps are the special case [[a, b], [0, 1]].  ``mat2_product`` folds
+  in FP64, ``mat2_exact`` in rationals, ``mat2_abs`` gives prod |M_x|
+  (entrywise absolute values), the scale of rounding errors.
+* the last valid value: the value of the last iteration that is not NaN
+  (NaN marks "no value"), NaN if there is none; combining: the later range's
+  value unless it is NaN.  Exact (values are copied, never computed).
 """
 from __future__ import annotations
 
@@ -91,3 +103,70 @@ def error_bound(k: int) -> float:
     fused multiply-add once."""
     u = 2.0 ** -24
     return 2 * k * u / (1.0 - 2 * k * u)
+
+
+# ---------------------------------------------------------------- 2x2 matrix products
+
+def mat2_combine(earlier, later):
+    """Adjacent ranges: `earlier` applied first, so the product is later @ earlier."""
+    (e00, e01, e10, e11), (l00, l01, l10, l11) = earlier, later
+    return (l00 * e00 + l01 * e10, l00 * e01 + l01 * e11, l10 * e00 + l11 * e10, l10 * e01 + l11 * e11)
+
+
+def mat2_product(m):
+    """M_{R-1} ... M_0 of one output, m of shape (R, 4) (row-major entries), FP64,
+    folded one iteration at a time in order."""
+    M = (1.0, 0.0, 0.0, 1.0)
+    for row in np.asarray(m, np.float64).reshape(-1, 4).tolist():
+        M = mat2_combine(M, tuple(row))
+    return M
+
+
+def mat2_rows(m3d):
+    """Every output of an (O, R, 4) array: (O, 4) in FP64 (vectorised over outputs)."""
+    m = np.asarray(m3d, np.float64)
+    O = m.shape[0]
+    M = np.tile(np.array([1.0, 0.0, 0.0, 1.0]), (O, 1))
+    for x in range(m.shape[1]):
+        l00, l01, l10, l11 = (m[:, x, i] for i in range(4))
+        e00, e01, e10, e11 = (M[:, i].copy() for i in range(4))
+        M[:, 0] = l00 * e00 + l01 * e10
+        M[:, 1] = l00 * e01 + l01 * e11
+        M[:, 2] = l10 * e00 + l11 * e10
+        M[:, 3] = l10 * e01 + l11 * e11
+    return M
+
+
+def mat2_exact(m):
+    """Exact rational product (small integer or dyadic entries)."""
+    M = (Fraction(1), Fraction(0), Fraction(0), Fraction(1))
+    for row in m:
+        M = mat2_combine(M, tuple(Fraction(v) for v in row))
+    return M
+
+
+def mat2_abs_rows(m3d):
+    """prod |M_x| per output: the entrywise scale of the rounding error bound."""
+    return mat2_rows(np.abs(np.asarray(m3d, np.float64)))
+
+
+# ---------------------------------------------------------------- last valid value
+
+def last_valid(v):
+    """The last value of v that is not NaN, NaN if there is none (scanning in order)."""
+    out = float("nan")
+    for x in np.asarray(v, np.float32).tolist():
+        if not np.isnan(x):
+            out = x
+    return out
+
+
+def last_valid_rows(v2d):
+    """Every row of an (O, R) array (float32 results, NaN where a row has no value)."""
+    v = np.asarray(v2d, np.float32)
+    out = np.full(v.shape[0], np.nan, np.float32)
+    for x in range(v.shape[1]):
+        col = v[:, x]
+        keep = ~np.isnan(col)
+        out[keep] = col[keep]
+    return out
