@@ -499,44 +499,63 @@ def run_stencil_workload(args):
 
 
 def run_ordered_workload(args):
-    """Ordered reduction with a non-commutative operator: 64 rows of 2^22 affine
-    maps (a uniform [0.9, 1) seed 12, b normal seed 13), each row composed in
-    iteration order (the last value of y = a y + b from 0, and the product of a).
-    Inputs (2 GiB) are larger than L2."""
+    """Ordered reductions with a non-commutative operator (--ordered-op), 64 rows:
+    compose: 2^22 affine maps per row (a uniform [0.9, 1) seed 12, b normal seed
+    13), composed in iteration order (the last value of y = a y + b from 0, and
+    the product of a); 2 GiB.  mat2: 2^21 two-state Markov matrices per row
+    [[1-p, p], [q, 1-q]] (p seed 12, q seed 13, uniform [0, 1)) multiplied in
+    order; 2 GiB.  last: 2^22 values per row (normal seed 13), 90% of them
+    missing (NaN where a uniform seed-12 draw < 0.9), the last value present;
+    1 GiB.  Inputs are larger than L2."""
     import torch
 
     from paper_2309_01906_gb300 import binding as hb
     from paper_2309_01906_gb300 import synth
-    O, R = args.ordered_rows, args.ordered_len
-    a = synth.uniform_f32(O * R, 0.9, 1.0, 12)
-    b = synth.normal_f32(O * R, 13)
-    da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
-    out = torch.empty(2 * O, dtype=torch.float32, device="cuda")
+    op = args.ordered_op
+    O, R = args.ordered_rows, args.ordered_len // (2 if op == "mat2" else 1)
+    u = torch.from_numpy(synth.uniform_f32(O * R, 0.9 if op == "compose" else 0.0, 1.0, 12)).cuda()
+    w = torch.from_numpy(synth.uniform_f32(O * R, 0.0, 1.0, 13) if op == "mat2" else synth.normal_f32(O * R, 13)).cuda()
+    if op == "compose":
+        ins, nout, ib = [u, w], 2, 8
+        what = "composition of affine maps in iteration order"
+    elif op == "mat2":
+        ins, nout, ib = [torch.stack([1 - u, u, w, 1 - w], dim=-1).contiguous()], 4, 16
+        what = "product of 2x2 Markov matrices in iteration order"
+    else:
+        ins, nout, ib = [torch.where(u < 0.9, torch.full_like(w, float("nan")), w)], 1, 4
+        what = "last value present (90% missing)"
+    del u, w
+    out = torch.empty(nout * O, dtype=torch.float32, device="cuda")
     stream = torch.cuda.Stream()
-    n = hb.Nest([O, R], 1, "compose", "f32", "load")
+    n = hb.Nest([O, R], 1, {"compose": "compose", "mat2": "mat2", "last": "last"}[op], "f32", "load")
     plan = n.describe()
-    ms = _event_time(lambda: n.run([da.data_ptr(), db.data_ptr()], out.data_ptr(), stream.cuda_stream), args.steps,
-                     args.warmup, stream)
+    ptrs = [t.data_ptr() for t in ins]
+    ms = _event_time(lambda: n.run(ptrs, out.data_ptr(), stream.cuda_stream), args.steps, args.warmup, stream)
     n.close()
     peak, kind = measured_peaks()
-    nbytes = 8 * O * R + 8 * O
+    nbytes = ib * O * R + 4 * nout * O
     gbs = nbytes / (ms * 1e-3) / 1e9
     cpu = None
     if not args.no_cpu_baseline:
         from oracle import ordered as oo
         m = min(R, 1 << 20)
+        row = [t[:m].cpu().numpy() for t in ins]
         t0 = time.perf_counter()
-        oo.compose(a[:m].astype(np.float64), b[:m].astype(np.float64))
+        if op == "compose":
+            oo.compose(row[0].astype(np.float64), row[1].astype(np.float64))
+        elif op == "mat2":
+            oo.mat2_product(row[0])
+        else:
+            oo.last_valid(row[0])
         dt = time.perf_counter() - t0
         cpu = {"value": m / dt, "unit": "iterations/s", "cores": 1, "kind": "oracle",
-               "sample": f"the first {m} maps of row 0, folded in FP64"}
-    print(json.dumps({"workload": f"ordered reduction {O} x {R}: composition of affine maps in iteration order",
+               "sample": f"the first {m} iterations of row 0, in order"}
+    print(json.dumps({"workload": f"ordered reduction {O} x {R}: {what}", "op": op,
                       "metric": "nest iterations/s", "value": O * R / (ms * 1e-3), "unit": "iterations/s",
                       "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup, "plan": plan,
                       "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                                    "peak_kind": kind, "algorithmic_bytes": nbytes},
-                      "cpu_baseline": cpu, "l2": "inputs (2 GiB) larger than L2; no flush"}))
-
+                      "cpu_baseline": cpu, "l2": f"inputs ({nbytes / 2**30:.1f} GiB) larger than L2; no flush"}))
 
 def run_narrow_workload(args):
     """Nests on 8- / 16-bit integers with SIMD-in-register sub-lanes: 1 GiB of
@@ -813,7 +832,9 @@ def main():
     ap.add_argument("--csr-rows", type=int, default=1 << 22)
     ap.add_argument("--stencil-n", type=int, default=16384, help="stencil: array side")
     ap.add_argument("--ordered-rows", type=int, default=64, help="ordered: rows (outputs)")
-    ap.add_argument("--ordered-len", type=int, default=1 << 22, help="ordered: maps per row")
+    ap.add_argument("--ordered-len", type=int, default=1 << 22, help="ordered: maps per row (half for mat2)")
+    ap.add_argument("--ordered-op", default="compose", choices=["compose", "mat2", "last"],
+                    help="ordered: the non-commutative operator")
     ap.add_argument("--narrow-rows", type=int, default=16384, help="narrow: rows (outputs) of 64 KiB")
     ap.add_argument("--narrow-cases", default="", help="narrow: comma list of cases to keep (e.g. i8_dot,i16_sum)")
     ap.add_argument("--stencil-steps", default="1,4", help="stencil: steps per launch to time (comma list)")

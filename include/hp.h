@@ -79,8 +79,12 @@ typedef enum hp_red_op {
     HP_RED_MAX = 1,
     HP_RED_MIN = 2,
     HP_RED_HIST_COUNT = 3,  /* CSR nests only: count histogram of col >> shift */
-    HP_RED_AFFINE_COMPOSE = 4  /* non-commutative: composition of affine maps in
+    HP_RED_AFFINE_COMPOSE = 4, /* non-commutative: composition of affine maps in
                                   iteration order (below) */
+    HP_RED_MAT2_PRODUCT = 5,   /* non-commutative: product of 2x2 matrices in
+                                  iteration order (below) */
+    HP_RED_LAST_VALID = 6      /* non-commutative: the last value that is not NaN
+                                  (below) */
 } hp_red_op;
 
 /*
@@ -100,6 +104,28 @@ typedef enum hp_red_op {
  * output) or GRID (tile > 0 on the first reduced level: parts of tile x the
  * deeper extents, one CTA each, folded in part order), or AUTO.  Not batched,
  * served, tuned or run from host buffers (HP_EUNSUPPORTED).
+ *
+ * HP_RED_MAT2_PRODUCT: the same lowering with 2x2 matrices.  in_dev = {m}, one
+ * FP32 array of 4 entries per iteration (row-major m00 m01 m10 m11, iteration
+ * x of the flat nest at m[4x .. 4x+3]); the output is M_{R-1} ... M_1 M_0 (the
+ * later matrix on the left), 4 floats per output.  Combining E then L gives
+ * L E, each entry as fma(l_i0, e_0j, l_i1 * e_1j).  Second-order linear
+ * recurrences y_x = p_x y_{x-1} + q_x y_{x-2} take the step [[p, q], [1, 0]];
+ * the affine maps are the case [[a, b], [0, 1]].
+ *
+ * Error bound of both (hp_nest_error_bound): gamma_{2(R-1)} relative to the
+ * product of the |M_x| (for affine maps: |A| and sum |b_x| prod_{z>x} |a_z|).
+ * R maps make R - 1 combines in any tree and the relative errors of all of them
+ * add (for products the count, not the depth of the tree, decides); infinite
+ * once 2 (R - 1) u >= 1.  Typical errors grow like sqrt(R) u.
+ *
+ * HP_RED_LAST_VALID: in_dev = {v}, one FP32 array of the nest's shape; NaN
+ * marks an iteration without a value.  The output (1 float) is the value of
+ * the last iteration in order that is not NaN, copied bit for bit, or the
+ * quiet NaN 0x7fc00000 when there is none (the final value of a forward fill).
+ * Exact (error bound 0).  Inputs 32-byte aligned with R (and grid parts) a
+ * whole number of 256-bit loads use them; 16-byte aligned, 128-bit loads;
+ * otherwise scalar loads, for every ordered operator.
  */
 
 /*

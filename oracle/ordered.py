@@ -36,6 +36,7 @@ Two more non-commutative operators of the same kind:
 """
 from __future__ import annotations
 
+import math
 from fractions import Fraction
 
 import numpy as np
@@ -97,12 +98,21 @@ def abs_bound_rows(a2d, b2d):
 
 
 def error_bound(k: int) -> float:
-    """gamma_{2k} = 2k u / (1 - 2k u), u = 2^-24: the first-order relative bound (on the
-    scales of ``abs_bound``) of an FP32 evaluation in which every element passes
-    through at most k folds or combines, each rounding its product once and its
-    fused multiply-add once."""
+    """gamma_{2k} = 2k u / (1 - 2k u), u = 2^-24: the worst-case relative bound (on the
+    scales of ``abs_bound`` / ``mat2_abs_rows``) of an FP32 evaluation that makes k
+    combines in all (R maps in any tree: k = R - 1), each rounding twice (a product
+    and a fused multiply-add).  For products the relative errors of every combine
+    add, whatever the tree's shape (a product of R numbers carries R - 1
+    roundings), so k counts all combines, not the depth of the tree."""
     u = 2.0 ** -24
     return 2 * k * u / (1.0 - 2 * k * u)
+
+
+def prob_bound(k: int, lam: float = 10.0) -> float:
+    """lam sqrt(2k) u: the probabilistic bound for the same evaluation, modelling the
+    2k rounding errors as independent, mean zero and bounded by u (a Hoeffding bound
+    on their weighted sum: it fails with probability below 2 exp(-lam^2 / 2))."""
+    return lam * math.sqrt(2 * max(k, 0)) * 2.0 ** -24
 
 
 # ---------------------------------------------------------------- 2x2 matrix products

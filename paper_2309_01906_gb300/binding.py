@@ -30,7 +30,8 @@ HP_MAX_DEPTH = 5
 
 HW = {"grid": HP_HW_GRID, "cluster": HP_HW_CLUSTER, "cta": HP_HW_CTA, "warp": HP_HW_WARP,
       "subwarp": HP_HW_SUBWARP, "lane": HP_HW_LANE, "seq": HP_HW_SEQ, "auto": HP_HW_AUTO}
-OPS = {"sum": HP_RED_SUM, "max": HP_RED_MAX, "min": HP_RED_MIN, "hist": HP_RED_HIST_COUNT, "compose": 4}
+OPS = {"sum": HP_RED_SUM, "max": HP_RED_MAX, "min": HP_RED_MIN, "hist": HP_RED_HIST_COUNT, "compose": 4,
+       "mat2": 5, "last": 6}
 PRECS = {"f32": HP_F32, "f32_comp": HP_F32_COMP, "i32": HP_I32, "i64": HP_I64, "i8": 4, "i16": 5}
 BODIES = {"load": HP_BODY_LOAD, "dot_bcast": HP_BODY_DOT_BCAST, "csr_gather": HP_BODY_CSR_GATHER,
           "affine": HP_BODY_AFFINE, "geometric": HP_BODY_GEOMETRIC}

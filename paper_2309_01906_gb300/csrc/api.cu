@@ -105,10 +105,12 @@ double error_bound(const hp_nest* n) {
   if (n->kind == NEST_RECT) return error_bound_rect(n->plan);
   if (n->kind == NEST_NARROW) return 0.0;   // integers: exact
   if (n->kind == NEST_ORDERED) {
-    // gamma_{2k}: every iteration passes through at most k folds or combines, each
-    // rounding one product and one fused multiply-add
-    const double u = std::ldexp(1.0, -24), k2 = 2.0 * n->ord.k;
-    return k2 * u / (1.0 - k2 * u);
+    if (n->ord.op == HP_RED_LAST_VALID) return 0.0;   // values are copied, never computed
+    // gamma_{2k}, k = R - 1: a product of R maps (or matrices) makes R - 1 combines
+    // in any tree, each rounding twice, and the relative errors of all of them add;
+    // no finite bound once 2k u reaches 1
+    const double u = std::ldexp(1.0, -24), k2 = 2.0 * static_cast<double>(std::max<int64_t>(n->ord.R - 1, 0));
+    return k2 * u < 1.0 ? k2 * u / (1.0 - k2 * u) : INFINITY;
   }
   if (n->csr.op != HP_RED_SUM || n->csr.prec != HP_F32_COMP) return n->csr.op == HP_RED_SUM ? 1e-5 : 0.0;
   return 1e-6;
@@ -132,7 +134,7 @@ hp_status tune_release_device(hp_nest* n) {
 
 size_t out_bytes(const hp_nest* n) {
   if (n->kind == NEST_RECT) return static_cast<size_t>(n->plan.rp.O) * n->plan.out_elem_bytes;
-  if (n->kind == NEST_ORDERED) return static_cast<size_t>(n->ord.O) * 2 * sizeof(float);
+  if (n->kind == NEST_ORDERED) return ordered_out_bytes(n->ord);
   if (n->kind == NEST_NARROW) return static_cast<size_t>(n->nar.O) * sizeof(int32_t);
   return csr_out_bytes(n);
 }
@@ -185,7 +187,7 @@ hp_status hp_nest_create(int depth, const int64_t* extents, const int64_t* csr_o
   if (prec == HP_I8 || prec == HP_I16) {
     n->kind = NEST_NARROW;
     st = plan_narrow(depth, extents, map, op, red_level, prec, body, &n->nar, &why);
-  } else if (op == HP_RED_AFFINE_COMPOSE) {
+  } else if (op == HP_RED_AFFINE_COMPOSE || op == HP_RED_MAT2_PRODUCT || op == HP_RED_LAST_VALID) {
     n->kind = NEST_ORDERED;
     st = plan_ordered(depth, extents, map, op, red_level, prec, body, &n->ord, &why);
   } else if (csr_offsets != nullptr || body == HP_BODY_CSR_GATHER || op == HP_RED_HIST_COUNT) {

@@ -58,6 +58,7 @@ hp_status plan_ordered(int depth, const int64_t* extents, const hp_level_map* ma
 std::string describe_ordered(const OrderedPlan& p);
 hp_status ordered_prepare(hp_nest* n);
 hp_status run_ordered(hp_nest* n, const void* const* in_dev, void* out_dev, cudaStream_t st);
+size_t ordered_out_bytes(const OrderedPlan& p);
 
 // nests on 8- / 16-bit integers (narrow.cu)
 hp_status plan_narrow(int depth, const int64_t* extents, const hp_level_map* map, hp_red_op op, int red_level,

@@ -113,8 +113,10 @@ struct OrderedPlan {
   int32_t W = 8;              // warps per CTA team
   int64_t G = 1, part = 0;    // grid parts per output, iterations per part
   int64_t chunk = 0;          // iterations per thread (a multiple of V)
-  int32_t V = 1;              // 8: 256-bit loads (R and part multiples of 8); 4: 128-bit loads (multiples of 4)
+  int32_t V = 1;              // load width: 8 = 256-bit, 4 = 128-bit, 1 = scalar (R and part whole loads)
   int32_t k = 0;              // longest chain of folds and combines of one iteration
+  int32_t op = HP_RED_AFFINE_COMPOSE;   // AFFINE_COMPOSE, MAT2_PRODUCT or LAST_VALID
+  int32_t ib = 4;             // bytes of one iteration in each input array (16: a 2x2 matrix)
 };
 
 // Plan of a nest on 8- or 16-bit integers (SIMD sub-lanes in 32-bit

@@ -310,22 +310,30 @@ int nar_blocks(K kernel, int threads, int sms) {
   return std::max(1, per) * sms;
 }
 
+// CTAs for `items` work items when `resident` fit at once: the fewest waves,
+// with the items spread evenly over them (no short last wave)
+int64_t balanced_grid(int64_t items, int64_t resident) {
+  if (items <= resident) return std::max<int64_t>(items, 1);
+  const int64_t waves = ceil_div64(items, resident);
+  return ceil_div64(items, waves);
+}
+
 template <class E, int OP, bool DOT, bool VEC>
 cudaError_t launch_narrow(const NarrowPlan& p, const NarArgs& g, int sms, cudaStream_t st) {
   if (p.team == 0) {
     const int64_t need = ceil_div64(p.O, kNarThreads / 32);
     const int grid =
-        static_cast<int>(std::min<int64_t>(need, nar_blocks(narrow_warp_kernel<E, OP, DOT, VEC>, kNarThreads, sms)));
+        static_cast<int>(balanced_grid(need, nar_blocks(narrow_warp_kernel<E, OP, DOT, VEC>, kNarThreads, sms)));
     narrow_warp_kernel<E, OP, DOT, VEC><<<grid, kNarThreads, 0, st>>>(g);
   } else {
     const int threads = 32 * p.W;
     if (threads <= kNarThreads) {
       auto k = narrow_block_kernel<E, OP, DOT, VEC, kNarThreads>;
-      const int grid = static_cast<int>(std::min<int64_t>(p.O * p.G, nar_blocks(k, threads, sms)));
+      const int grid = static_cast<int>(balanced_grid(p.O * p.G, nar_blocks(k, threads, sms)));
       k<<<grid, threads, 0, st>>>(g);
     } else {
       auto k = narrow_block_kernel<E, OP, DOT, VEC, 1024>;
-      const int grid = static_cast<int>(std::min<int64_t>(p.O * p.G, nar_blocks(k, threads, sms)));
+      const int grid = static_cast<int>(balanced_grid(p.O * p.G, nar_blocks(k, threads, sms)));
       k<<<grid, threads, 0, st>>>(g);
     }
   }

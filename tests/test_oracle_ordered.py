@@ -86,9 +86,27 @@ def test_fp32_tree_within_the_bound():
                  for p1, p2 in zip(parts[0::2], parts[1::2])]
     A, B = oo.compose(a32.astype(np.float64), b32.astype(np.float64))
     Aa, Ba = oo.abs_bound(a32.astype(np.float64), b32.astype(np.float64))
-    k = 16 + int(math.log2(64))
+    k = 1023   # combines in all: the relative errors of every combine add
     assert abs(float(parts[0][0]) - A) <= oo.error_bound(k) * Aa
     assert abs(float(parts[0][1]) - B) <= oo.error_bound(k) * Ba
+    assert abs(float(parts[0][0]) - A) <= oo.prob_bound(k) * Aa
+    assert abs(float(parts[0][1]) - B) <= oo.prob_bound(k) * Ba
+
+
+def test_product_errors_add_over_every_combine():
+    # R equal factors multiplied in a balanced FP32 tree of depth log2 R: every
+    # level squares the partial products and doubles the relative error they
+    # carry, so the error grows with the number of combines (R - 1), far beyond
+    # what a bound on the depth of the tree would allow
+    a32 = np.float32(1.0 + 2.0 ** -12 + 3 * 2.0 ** -23)
+    R = 1 << 14
+    v = [a32] * R
+    while len(v) > 1:
+        v = [np.float32(v[i] * v[i + 1]) for i in range(0, len(v), 2)]
+    exact = math.exp(R * math.log1p(float(a32) - 1.0))
+    rel = abs(float(v[0]) - exact) / exact
+    assert rel <= oo.error_bound(R - 1)
+    assert rel > 100 * oo.error_bound(14)
 
 
 # ---- planted mistakes

@@ -58,5 +58,5 @@ def test_ordered_nests_are_not_batched_or_tuned():
     with pytest.raises(hb.HPError) as e:
         n.tune([0x1000, 0x2000], 0x3000)
     assert e.value.status == hb.HP_EUNSUPPORTED
-    assert 0 < n.error_bound() < 1e-5
+    assert n.error_bound() == pytest.approx(2 * 99 * 2.0 ** -24, rel=1e-4)   # gamma_{2(R-1)}, R = 100
     n.close()
