@@ -23,6 +23,8 @@
 // integer atomics (exact in any order), fused into the same sweep or alone.
 // An explicit map for the entry level (SEQ, SUBWARP(w), WARP, CTA) puts every
 // row into that one class instead.
+// The x gathers are random 4-byte reads that L1 almost never serves again, so
+// they are cached in L2 only (__ldcg): no L1 line fills for single use.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -283,7 +285,7 @@ __device__ __forceinline__ void csr_fold(const CsrArgs& a, int* sh, int64_t s, i
     for (int u = 0; u < 4; ++u) {
       if (ok[u]) {
         if (static_cast<uint32_t>(c[u]) < static_cast<uint64_t>(a.n_cols)) {
-          Op::add_prod(acc[u], v[u], __ldg(a.x + c[u]));
+          Op::add_prod(acc[u], v[u], __ldcg(a.x + c[u]));
           if constexpr (HIST) hist_add(a, sh, c[u]);
         } else {
           atomicExch(a.err, 2);
@@ -298,7 +300,7 @@ __device__ __forceinline__ void csr_fold_one(const CsrArgs& a, int* sh, int64_t 
   const int32_t c = __ldcs(a.col + idx);
   const float v = __ldcs(a.val + idx);
   if (static_cast<uint32_t>(c) < static_cast<uint64_t>(a.n_cols)) {
-    Op::add_prod(acc, v, __ldg(a.x + c));
+    Op::add_prod(acc, v, __ldcg(a.x + c));
     if constexpr (HIST) hist_add(a, sh, c);
   } else {
     atomicExch(a.err, 2);
@@ -313,7 +315,7 @@ __device__ __forceinline__ void csr_fold_group(const CsrArgs& a, int* sh, const 
   float xv[4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
-    xv[u] = (static_cast<uint32_t>(cc[u]) < static_cast<uint64_t>(a.n_cols)) ? __ldg(a.x + cc[u]) : 0.0f;
+    xv[u] = (static_cast<uint32_t>(cc[u]) < static_cast<uint64_t>(a.n_cols)) ? __ldcg(a.x + cc[u]) : 0.0f;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     if (static_cast<uint32_t>(cc[u]) < static_cast<uint64_t>(a.n_cols)) {
