@@ -112,7 +112,8 @@ struct OrderedPlan {
   int32_t team = 0;           // 0: a warp per output; 1: a CTA of W warps per part
   int32_t W = 8;              // warps per CTA team
   int64_t G = 1, part = 0;    // grid parts per output, iterations per part
-  int64_t chunk = 0;          // iterations per thread (a multiple of V)
+  int64_t chunk = 0;          // iterations per warp (a multiple of piece)
+  int64_t piece = 8;          // a lane's iterations per round (rounds of 32 pieces per warp)
   int32_t V = 1;              // load width: 8 = 256-bit, 4 = 128-bit, 1 = scalar (R and part whole loads)
   int32_t k = 0;              // longest chain of folds and combines of one iteration
   int32_t op = HP_RED_AFFINE_COMPOSE;   // AFFINE_COMPOSE, MAT2_PRODUCT or LAST_VALID

@@ -127,16 +127,21 @@ hp_status plan_ordered(int depth, const int64_t* extents, const hp_level_map* ma
   for (int l = 0; l < depth; ++l)
     p.map[l] = {l < red_level ? HP_HW_GRID : red_hw, l >= red_level && red_hw == HP_HW_CTA ? p.W : 0,
                 l == red_level && red_hw == HP_HW_GRID ? p.part / inner : 0};
-  const int64_t threads = p.team == 0 ? 32 : 32 * static_cast<int64_t>(p.W);
   if (p.ib == 16)   // a matrix is one 128-bit load; two make one 256-bit load
     p.V = (R % 2 == 0 && p.part % 2 == 0) ? 8 : 4;
   else
     p.V = (R % 8 == 0 && p.part % 8 == 0) ? 8 : ((R % 4 == 0 && p.part % 4 == 0) ? 4 : 1);
-  p.chunk = std::max<int64_t>(1, ceil_div(std::max<int64_t>(p.part, 1), threads));
-  const int64_t per_load = std::max(1, 4 * p.V / p.ib);   // iterations in one widest load
-  p.chunk = ceil_div(p.chunk, per_load) * per_load;
-  // longest chain: the thread's block, 5 lane levels, 5 warp levels (CTA teams), the part fold
-  p.k = static_cast<int32_t>(std::min<int64_t>(p.chunk + 5 + (p.team ? 5 : 0) + (p.G - 1), int64_t(1) << 30));
+  // a lane's piece of each round, measured per operator: 8 affine maps (32 bytes
+  // of each input: a warp's load reads 1 KB in one piece), 4 matrices, 32 values
+  // (fewer rounds where the butterfly or the round's latency costs more than
+  // coalescing gains); a warp's range is a whole number of pieces
+  p.piece = op == HP_RED_MAT2_PRODUCT ? 4 : (op == HP_RED_LAST_VALID ? 32 : 8);
+  p.chunk = p.team == 0 ? std::max<int64_t>(R, 1) : ceil_div(std::max<int64_t>(p.part, 1), p.W);
+  p.chunk = ceil_div(p.chunk, p.piece) * p.piece;
+  // longest chain: a piece, 5 lane levels, the rounds, 5 warp levels (CTA teams), the part fold
+  const int64_t rounds = ceil_div(p.chunk, 32 * p.piece);
+  p.k = static_cast<int32_t>(
+      std::min<int64_t>(p.piece + 5 + rounds + (p.team ? 5 : 0) + (p.G - 1), int64_t(1) << 30));
   *out = p;
   return HP_OK;
 }
@@ -154,7 +159,8 @@ std::string describe_ordered(const OrderedPlan& p) {
       << ",\"tile\":" << p.map[l].tile << "}";
   s << "],\"auto_map\":" << (p.auto_map ? "true" : "false") << ",\"team\":\"" << (p.team ? "block" : "warp")
     << "\",\"outputs\":" << p.O << ",\"reduced\":" << p.R << ",\"warps\":" << p.W << ",\"grid_parts\":" << p.G
-    << ",\"part\":" << p.part << ",\"chunk\":" << p.chunk << ",\"vec\":" << p.V << ",\"chain\":" << p.k
+    << ",\"part\":" << p.part << ",\"chunk\":" << p.chunk << ",\"piece\":" << p.piece << ",\"vec\":" << p.V
+    << ",\"chain\":" << p.k
     << ",\"kernel\":\"ordered_" << (p.team ? "block" : "warp") << "\"}";
   return s.str();
 }
@@ -186,6 +192,8 @@ __device__ __forceinline__ void ld8(const float* p, float* r) {
 struct AffineOp {
   using S = float2;   // (A, B)
   static constexpr int kOut = 2;
+  template <int V>
+  __device__ static constexpr int64_t piece() { return 8; }   // a lane's iterations per round
   __device__ static S ident() { return make_float2(1.0f, 0.0f); }
   __device__ static S combine(S e, S l) { return make_float2(__fmul_rn(l.x, e.x), __fmaf_rn(l.x, e.y, l.y)); }
   __device__ static S shfl(S v, int m) {
@@ -258,6 +266,8 @@ __device__ __forceinline__ AffineOp::S AffineOp::fold(const OrdArgs& g, int64_t 
 struct Mat2Op {
   using S = float4;   // (m00, m01, m10, m11)
   static constexpr int kOut = 4;
+  template <int V>
+  __device__ static constexpr int64_t piece() { return 4; }
   __device__ static S ident() { return make_float4(1.0f, 0.0f, 0.0f, 1.0f); }
   __device__ static S combine(S e, S l) {   // L E
     return make_float4(__fmaf_rn(l.x, e.x, __fmul_rn(l.y, e.z)), __fmaf_rn(l.x, e.y, __fmul_rn(l.y, e.w)),
@@ -315,6 +325,8 @@ struct Mat2Op {
 struct LastOp {
   using S = float;    // the last value that is not NaN so far (NaN: none)
   static constexpr int kOut = 1;
+  template <int V>
+  __device__ static constexpr int64_t piece() { return 32; }
   __device__ static S ident() { return __int_as_float(0x7fc00000); }
   __device__ static S combine(S e, S l) { return l != l ? e : l; }
   __device__ static S shfl(S v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
@@ -374,14 +386,30 @@ __device__ __forceinline__ typename Op::S lanes_in_order(typename Op::S v, int l
   return v;
 }
 
+// A warp folds its range [ws, we) in rounds of 32 consecutive pieces of P
+// iterations: lane l folds the l-th piece (so one load instruction of the
+// warp reads 32 adjacent pieces: coalesced), the butterfly joins the 32 pieces
+// in order, and the round joins the running state.  Every lane ends with the
+// composition of the whole range.
+template <class Op, int V>
+__device__ __forceinline__ typename Op::S fold_warp(const OrdArgs& g, int64_t base, int64_t ws, int64_t we, int lane) {
+  constexpr int64_t P = Op::template piece<V>();
+  typename Op::S v = Op::ident();
+  for (int64_t r0 = ws; r0 < we; r0 += 32 * P) {
+    const int64_t s = std::min<int64_t>(r0 + lane * P, we), e = std::min<int64_t>(s + P, we);
+    typename Op::S pc = Op::template fold<V>(g, base, s, e, Op::ident());
+    pc = lanes_in_order<Op>(pc, lane);
+    v = Op::combine(v, pc);
+  }
+  return v;
+}
+
 template <class Op, int V>
 __global__ void __launch_bounds__(kOrdThreads) ordered_warp_kernel(OrdArgs g) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = static_cast<int64_t>(gridDim.x) * (kOrdThreads / 32);
   for (int64_t o = static_cast<int64_t>(blockIdx.x) * (kOrdThreads / 32) + (threadIdx.x >> 5); o < g.O; o += warps) {
-    const int64_t s = std::min<int64_t>(lane * g.chunk, g.R), e = std::min<int64_t>(s + g.chunk, g.R);
-    typename Op::S v = Op::template fold<V>(g, o * g.R, s, e, Op::ident());
-    v = lanes_in_order<Op>(v, lane);
+    const typename Op::S v = fold_warp<Op, V>(g, o * g.R, 0, g.R, lane);
     if (lane == 0) Op::put(g.out, o, v);
   }
 }
@@ -394,9 +422,8 @@ __global__ void __launch_bounds__(1024) ordered_block_kernel(OrdArgs g) {   // W
   for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
     const int64_t o = item / g.G, pg = item - o * g.G;
     const int64_t lo = pg * g.part_len, hi = std::min<int64_t>(lo + g.part_len, g.R);
-    const int64_t s = std::min<int64_t>(lo + threadIdx.x * g.chunk, hi), e = std::min<int64_t>(s + g.chunk, hi);
-    typename Op::S v = Op::template fold<V>(g, o * g.R, s, e, Op::ident());
-    v = lanes_in_order<Op>(v, lane);
+    const int64_t ws = std::min<int64_t>(lo + warp * g.chunk, hi), we = std::min<int64_t>(ws + g.chunk, hi);
+    const typename Op::S v = fold_warp<Op, V>(g, o * g.R, ws, we, lane);
     if (lane == 0) wp[warp] = v;
     __syncthreads();
     if (warp == 0) {

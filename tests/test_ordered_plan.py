@@ -13,27 +13,41 @@ def plan(ext, r, lm=None):
 
 
 def test_auto_teams():
+    # chunk: iterations per warp (whole pieces); a warp folds its range in rounds of
+    # 32 pieces, one per lane
     d = plan([1000, 300], 1)
-    assert d["kind"] == "ordered" and d["team"] == "warp" and d["chunk"] == 12 and d["grid_parts"] == 1   # 300/32 -> 4s
-    assert d["vec"] == 4                                  # 300 is a multiple of 4, not of 8
+    assert d["kind"] == "ordered" and d["team"] == "warp" and d["grid_parts"] == 1
+    assert d["piece"] == 8 and d["chunk"] == 304 and d["vec"] == 4   # 300 is a multiple of 4, not of 8
     d = plan([1000, 5000], 1)
-    assert d["team"] == "block" and d["warps"] == 8 and d["grid_parts"] == 1 and d["chunk"] == 24   # 5000/256 -> 8s
+    assert d["team"] == "block" and d["warps"] == 8 and d["grid_parts"] == 1 and d["chunk"] == 632   # 5000/8 -> 8s
     assert d["vec"] == 8
     d = plan([4, 1 << 22], 1)
     assert d["team"] == "block" and d["grid_parts"] > 1 and d["part"] * (d["grid_parts"] - 1) < (1 << 22)
-    assert d["vec"] == 8 and d["chunk"] % 8 == 0 and d["part"] % 8 == 0
-    assert d["chain"] == d["chunk"] + 5 + 5 + d["grid_parts"] - 1
+    assert d["vec"] == 8 and d["chunk"] % d["piece"] == 0 and d["part"] % 8 == 0
+    rounds = -(-d["chunk"] // (32 * d["piece"]))
+    assert d["chain"] == d["piece"] + 5 + rounds + 5 + d["grid_parts"] - 1
+    assert plan([64, 4096], 1, ["grid", ("cta", 8, 0)])["piece"] == 8
+
+
+def test_pieces_per_operator():
+    def p(op, R):
+        n = hb.Nest([16, R], 1, op, "f32", "load")
+        d = n.describe()
+        n.close()
+        return d
+    assert p("mat2", 4096)["piece"] == 4 and p("mat2", 4096)["vec"] == 8 and p("mat2", 4095)["vec"] == 4
+    assert p("last", 4096)["piece"] == 32 and p("last", 4096)["chunk"] % 32 == 0
 
 
 def test_explicit_maps():
     d = plan([64, 3, 1000], 1, ["grid", ("cta", 4, 0), ("cta", 4, 0)])
-    assert d["team"] == "block" and d["warps"] == 4 and d["chunk"] == -(-3000 // 128)
+    assert d["team"] == "block" and d["warps"] == 4 and d["chunk"] == 752   # 3000 / 4 warps -> 8s
     d = plan([64, 3, 1000], 1, ["grid", ("grid", 0, 1), "grid"])
     assert d["grid_parts"] == 3 and d["part"] == 1000
     d = plan([8, 100], 1, ["grid", "warp"])
-    assert d["team"] == "warp" and d["chunk"] == 4
+    assert d["team"] == "warp" and d["chunk"] == 104
     d = plan([8, 102], 1, ["grid", "warp"])
-    assert d["vec"] == 1 and d["chunk"] == 4
+    assert d["vec"] == 1 and d["chunk"] == 104
 
 
 @pytest.mark.parametrize("kw,frag", [
