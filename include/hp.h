@@ -97,9 +97,10 @@ typedef enum hp_red_op {
  * iteration order F = f_{R-1} o ... o f_0, written as the pair (A, B) with
  * F(y) = A * y + B: B is the last value of the recurrence y_x = a_x y_{x-1} + b_x
  * from y = 0, A the product of the a_x.  out_dev: 2 floats per output (A, B).
- * Every thread folds a contiguous range of iterations (A <- a A, B <- fma(a, B,
- * b)); lanes, warps and grid parts are combined in iteration order: (A2, B2)
- * after (A1, B1) gives (A2 A1, fma(A2, B1, B2)).  Level map: outputs on GRID,
+ * Every warp folds a contiguous range of iterations in rounds of 32
+ * consecutive pieces, one per lane (A <- a A, B <- fma(a, B, b) within a
+ * piece); pieces, rounds, warps and grid parts are combined in iteration
+ * order: (A2, B2) after (A1, B1) gives (A2 A1, fma(A2, B1, B2)).  Level map: outputs on GRID,
  * the reduced levels on WARP (a warp per output), CTA (sub_width warps per
  * output) or GRID (tile > 0 on the first reduced level: parts of tile x the
  * deeper extents, one CTA each, folded in part order), or AUTO.  Not batched,

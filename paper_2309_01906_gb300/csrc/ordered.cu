@@ -2,13 +2,14 @@
 //
 // Sec. 2: a reduction combines on each level the results of its sibling
 // tasks; with a non-commutative operator the siblings must be combined in the
-// order of the iterations they folded.  The lowering therefore gives every
-// thread a contiguous block of iterations (not the cyclic slots of the other
-// reductions), folds it sequentially, and combines lanes, warps and grid parts
-// by rank: an xor butterfly whose masks grow 1, 2, ..., 16 combines at each
-// level two adjacent ranks, the lower one first (Sec. 3.7's sibling exchange),
-// and the parts of an output are folded in part order by the CTA that takes
-// the last ticket.
+// order of the iterations they folded.  The lowering gives every warp a
+// contiguous range of iterations and folds it in rounds: in each round lane l
+// folds the l-th of 32 consecutive pieces sequentially (so the warp's loads
+// are coalesced), an xor butterfly whose masks grow 1, 2, ..., 16 joins the 32
+// pieces, at each level two adjacent ranks with the lower one first (Sec.
+// 3.7's sibling exchange), and the round joins the warp's running state.
+// Warps of a CTA are combined by rank the same way, and the parts of an output
+// are folded in part order by the CTA that takes the last ticket.
 //
 // The operator is a compile-time parameter of the kernels (the op table):
 //   HP_RED_AFFINE_COMPOSE  f_x(y) = a_x y + b_x composed in order; (A1, B1) then
