@@ -198,7 +198,7 @@ struct AffineOp {
   __device__ static S ident() { return make_float2(1.0f, 0.0f); }
   __device__ static S combine(S e, S l) { return make_float2(__fmul_rn(l.x, e.x), __fmaf_rn(l.x, e.y, l.y)); }
   __device__ static S shfl(S v, int m) {
-    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+    return make_float2(__shfl_down_sync(0xffffffffu, v.x, m), __shfl_down_sync(0xffffffffu, v.y, m));
   }
   __device__ static void put(float* p, int64_t i, S v) {
     p[2 * i] = v.x;
@@ -275,8 +275,8 @@ struct Mat2Op {
                        __fmaf_rn(l.z, e.x, __fmul_rn(l.w, e.z)), __fmaf_rn(l.z, e.y, __fmul_rn(l.w, e.w)));
   }
   __device__ static S shfl(S v, int m) {
-    return make_float4(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m),
-                       __shfl_xor_sync(0xffffffffu, v.z, m), __shfl_xor_sync(0xffffffffu, v.w, m));
+    return make_float4(__shfl_down_sync(0xffffffffu, v.x, m), __shfl_down_sync(0xffffffffu, v.y, m),
+                       __shfl_down_sync(0xffffffffu, v.z, m), __shfl_down_sync(0xffffffffu, v.w, m));
   }
   __device__ static void put(float* p, int64_t i, S v) {
     p[4 * i] = v.x;
@@ -330,7 +330,7 @@ struct LastOp {
   __device__ static constexpr int64_t piece() { return 32; }
   __device__ static S ident() { return __int_as_float(0x7fc00000); }
   __device__ static S combine(S e, S l) { return l != l ? e : l; }
-  __device__ static S shfl(S v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+  __device__ static S shfl(S v, int m) { return __shfl_down_sync(0xffffffffu, v, m); }
   __device__ static void put(float* p, int64_t i, S v) { p[i] = v; }
   __device__ static S get(const volatile float* p, int64_t i) { return p[i]; }
   template <int V>
@@ -374,23 +374,23 @@ struct LastOp {
   }
 };
 
-// ranks 0..31 combined in rank order: at mask m the lower rank of each pair
-// comes first; both partners compute the same pair, so every lane ends with
-// the combination of all 32 ranges
+// ranks 0..31 combined in rank order into lane 0: at distance m lane l (a
+// multiple of 2m) holds ranks [l, l + m) and takes [l + m, l + 2m) from lane
+// l + m, its own range first.  Only lane 0's result is meaningful (the other
+// lanes combine ranges that are not adjacent); it is the same tree as an xor
+// butterfly's lane 0, with one combine per level and no selects.
 template <class Op>
 __device__ __forceinline__ typename Op::S lanes_in_order(typename Op::S v, int lane) {
+  (void)lane;
 #pragma unroll
-  for (int m = 1; m < 32; m <<= 1) {
-    const typename Op::S o = Op::shfl(v, m);
-    v = (lane & m) ? Op::combine(o, v) : Op::combine(v, o);
-  }
+  for (int m = 1; m < 32; m <<= 1) v = Op::combine(v, Op::shfl(v, m));
   return v;
 }
 
 // A warp folds its range [ws, we) in rounds of 32 consecutive pieces of P
 // iterations: lane l folds the l-th piece (so one load instruction of the
-// warp reads 32 adjacent pieces: coalesced), the butterfly joins the 32 pieces
-// in order, and the round joins the running state.  Every lane ends with the
+// warp reads 32 adjacent pieces: coalesced), the lane tree joins the 32 pieces
+// in order, and the round joins the running state.  Lane 0 ends with the
 // composition of the whole range.
 template <class Op, int V>
 __device__ __forceinline__ typename Op::S fold_warp(const OrdArgs& g, int64_t base, int64_t ws, int64_t we, int lane) {
