@@ -16,6 +16,14 @@ Metric: nest iterations per second (2^29 iterations per step).
 (each step a bounded sample of the same workload).  With N > 1 (torchrun) each
 rank runs an independent replica (no data exchange); value = all ranks'
 iterations / max over ranks of the timed region.
+
+Other workloads (--workload; one JSON line each, with rooflines; not the
+headline):  gemv (1024 x 1024, cold and warm), csr (Zipf(1.5) ragged rows with
+the fused histogram), batch (10,000 uneven nests in one persistent launch),
+serve (Poisson arrivals through the serving loop), stencil (16384^2 with ghost
+zones, 1 and 4 fused steps), ordered (non-commutative reductions:
+--ordered-op compose | mat2 | last), narrow (int8 / int16 nests with
+SIMD-in-register sub-lanes).
 """
 from __future__ import annotations
 

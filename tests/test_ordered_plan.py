@@ -74,3 +74,22 @@ def test_ordered_nests_are_not_batched_or_tuned():
     assert e.value.status == hb.HP_EUNSUPPORTED
     assert n.error_bound() == pytest.approx(2 * 99 * 2.0 ** -24, rel=1e-4)   # gamma_{2(R-1)}, R = 100
     n.close()
+
+
+def test_error_bound_of_products_counts_every_combine():
+    # gamma_{2(R-1)}: the relative errors of all R - 1 combines add, whatever the tree
+    u = 2.0 ** -24
+    for R in (1, 2, 1000, 1 << 20):
+        n = hb.Nest([3, R], 1, "compose", "f32", "load")
+        k2 = 2 * (R - 1)
+        assert n.error_bound() == pytest.approx(k2 * u / (1 - k2 * u), rel=1e-12, abs=0.0)
+        n.close()
+        m = hb.Nest([3, R], 1, "mat2", "f32", "load")
+        assert m.error_bound() == pytest.approx(k2 * u / (1 - k2 * u), rel=1e-12, abs=0.0)
+        m.close()
+    big = hb.Nest([1, (1 << 23) + 2], 1, "compose", "f32", "load")   # 2 (R - 1) u >= 1: no finite bound
+    assert big.error_bound() == float("inf")
+    big.close()
+    last = hb.Nest([3, 1000], 1, "last", "f32", "load")
+    assert last.error_bound() == 0.0
+    last.close()
