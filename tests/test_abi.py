@@ -159,3 +159,42 @@ def test_serving_needs_a_gpu():
     hb.hp_set_option("serve_batching", 0)
     assert hb.hp_get_option("serve_batching") == 0
     hb.hp_set_option("serve_batching", 1)
+
+
+def _header_enums():
+    """name -> value of every enumerator in include/hp.h (explicit values and
+    implicit successors, including 1u << k)."""
+    text = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "hp.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    vals = {}
+    for body in re.findall(r"typedef enum\s*\w*\s*\{(.*?)\}", text, flags=re.S):
+        nxt = 0
+        for item in [x.strip() for x in body.split(",") if x.strip()]:
+            if "=" in item:
+                name, expr = [t.strip() for t in item.split("=", 1)]
+                m = re.fullmatch(r"(\d+)u?\s*<<\s*(\d+)", expr)   # the header's two forms: N and 1u << k
+                v = int(m.group(1)) << int(m.group(2)) if m else int(expr.rstrip("u"))
+            else:
+                name, v = item, nxt
+            vals[name] = v
+            nxt = v + 1
+    return vals
+
+
+def test_binding_enums_match_the_header():
+    e = _header_enums()
+    for name, v in hb.HW.items():
+        assert e["HP_HW_" + name.upper()] == v
+    ops = {"sum": "HP_RED_SUM", "max": "HP_RED_MAX", "min": "HP_RED_MIN", "hist": "HP_RED_HIST_COUNT",
+           "compose": "HP_RED_AFFINE_COMPOSE", "mat2": "HP_RED_MAT2_PRODUCT", "last": "HP_RED_LAST_VALID"}
+    assert set(ops) == set(hb.OPS)
+    for k, name in ops.items():
+        assert e[name] == hb.OPS[k], k
+    for k, v in hb.PRECS.items():
+        assert e["HP_" + k.upper()] == v, k
+    for k, v in hb.BODIES.items():
+        assert e["HP_BODY_" + k.upper()] == v, k
+    for k, v in hb.PROPS.items():
+        assert e["HP_PROP_" + k.upper()] == v, k
+    for i, name in enumerate(hb.STATUS_NAMES):
+        assert e[name] == i
