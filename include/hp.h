@@ -253,6 +253,11 @@ hp_status hp_nest_create(int depth, const int64_t *extents, const int64_t *csr_o
  * The first run on a device allocates the nest's scratch; later runs allocate
  * nothing.  Asynchronous: returns after enqueueing.  Device-side errors
  * (a bounded wait that ran out) are reported by hp_nest_check.
+ * Concurrency: runs of one nest share its scratch (grid-part partials and,
+ * for ordered and narrow nests split over parts, per-output tickets), so
+ * runs of the same nest must be ordered (one stream, or events between
+ * streams); different nests may run concurrently on any streams.  A nest
+ * object is not thread-safe; give each host thread its own, or lock.
  */
 hp_status hp_nest_run(hp_nest *n, const void *const *in_dev, void *out_dev, void *stream);
 
