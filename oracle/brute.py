@@ -60,3 +60,31 @@ def rect(extents, red_level, op, prec, body, A=None, w=None, params=None):
             v = min(terms, default=ident)
         results.append(v)
     return results
+
+
+def rect_conditioning(extents, red_level, body, A=None, w=None, params=None):
+    """Per output, the exactly rounded sum|t| and sum t^2 of its FP body values.
+
+    The conditioning of a sum (Sec. 2's recursive reduction reaches the exact
+    sum only up to rounding; its error scales with these two quantities).  Each
+    t is formed in FP64 as in the C oracle (a product of two FP32 numbers is
+    exact there); the sums use ``math.fsum``.
+    """
+    d = len(extents)
+    out_ext = extents[:red_level]
+    red_ext = extents[red_level:]
+    abs_sums, sq_sums = [], []
+    for oi in itertools.product(*[range(n) for n in out_ext]):
+        ts = []
+        for ri in itertools.product(*[range(n) for n in red_ext]):
+            idx = tuple(oi) + tuple(ri)
+            flat = 0
+            for l in range(d):
+                flat = flat * extents[l] + idx[l]
+            rflat = 0
+            for l, i in enumerate(ri):
+                rflat = rflat * red_ext[l] + i
+            ts.append(_body(body, flat, rflat, A, w, params, False))
+        abs_sums.append(math.fsum(abs(t) for t in ts))
+        sq_sums.append(math.fsum(t * t for t in ts))
+    return abs_sums, sq_sums

@@ -48,7 +48,9 @@ enum { ORC_BODY_LOAD = 0, ORC_BODY_DOT_BCAST = 1, ORC_BODY_AFFINE = 3, ORC_BODY_
  * value the oracle library is ever built with outside those checks) leaves
  * every formula as written.  1 drops the last term of each innermost loop,
  * 2 negates odd-indexed terms, 3 transposes the broadcast operand's index,
- * 4 drops the Neumaier compensation, 5 reduces one level too few. */
+ * 4 drops the Neumaier compensation, 5 reduces one level too few,
+ * 6 doubles sum|t|, 7 adds |t| instead of t^2 to sum t^2, 8 adds t instead of
+ * |t| to sum|t|. */
 #ifndef ORACLE_MUTATION
 #define ORACLE_MUTATION 0
 #endif
@@ -89,8 +91,10 @@ static void fp_add(fp_acc *a, int op, double t)
     } else {
         if (t < a->best) a->best = t;
     }
-    a->abs_sum += fabs(t);
-    a->sq_sum += t * t;
+    if (ORACLE_MUTATION == 6) a->abs_sum += 2.0 * fabs(t);
+    else if (ORACLE_MUTATION == 8) a->abs_sum += t;
+    else a->abs_sum += fabs(t);
+    a->sq_sum += (ORACLE_MUTATION == 7) ? fabs(t) : t * t;
     a->count += 1;
 }
 

@@ -15,7 +15,11 @@ mismatch.  What pins what:
 * brute force: every nest of depth <= 3 with extents <= 3 against pure-Python
   loops (oracle/brute.py), both oracle formulations;
 * the paper's worked examples (tests/golden/paper_examples.json): structure only,
-  since the paper prints no result values.
+  since the paper prints no result values;
+* the conditioning sums sum|t| and sum t^2 that every FP result carries (they
+  set the scale of every FP tolerance): closed forms of integer-valued and
+  geometric bodies, numpy / scipy reductions of the FP64 body values, and the
+  pure-Python formulation.
 """
 from __future__ import annotations
 
@@ -305,6 +309,123 @@ def pin_paper_examples(lib):
     assert np.all(cover == 1)
 
 
+def _affine_power_sums(lo: int, hi: int, a: int, b: int, m: int):
+    """Exact sum|t| and sum t^2 of t = a + b (f mod m) over f in [lo, hi), by residue counts."""
+    s1 = s2 = 0
+    for k in range(m):
+        # number of f in [lo, hi) with f mod m == k
+        cnt = (hi - 1 - k) // m - (lo - 1 - k) // m if hi > lo else 0
+        t = a + b * k
+        s1 += cnt * abs(t)
+        s2 += cnt * t * t
+    return s1, s2
+
+
+def pin_conditioning_closed_forms(lib):
+    """sum|t| and sum t^2 of integer-valued AFFINE bodies are exact integers below
+    2^53, so every FP64 partial is exact: compare bit for bit with the closed
+    form from residue counts, for every op and every reduction level."""
+    for a, b, m in ((-7, 3, 11), (2, 5, 7), (-40, 9, 9)):
+        for ext in SHAPES:
+            d = len(ext)
+            for r in range(d + 1):
+                O = int(np.prod(ext[:r])) if r else 1
+                R = int(np.prod(ext[r:])) if r < d else 1
+                want = [_affine_power_sums(o * R, (o + 1) * R, a, b, m) for o in range(O)]
+                for op in ("sum", "max"):
+                    for fn in (oracle.rect, oracle.rect_flat):
+                        res = fn(ext, r, op, "f32", "affine", params=[a, b, m], lib=lib)
+                        assert [int(v) for v in res.abs_sum] == [w[0] for w in want], ("abs_sum", fn.__name__, ext, r, op)
+                        assert [int(v) for v in res.sq_sum] == [w[1] for w in want], ("sq_sum", fn.__name__, ext, r, op)
+                        assert np.all(res.abs_sum == np.rint(res.abs_sum)) and np.all(res.sq_sum == np.rint(res.sq_sum))
+    # geometric q^k with 0 < q < 1: every term positive, so sum|t| equals the
+    # geometric closed form and sum t^2 the closed form of the ratio q^2
+    q, m = Fraction(1, 2), 24
+    for ext in SHAPES:
+        d = len(ext)
+        for r in range(d + 1):
+            O = int(np.prod(ext[:r])) if r else 1
+            R = int(np.prod(ext[r:])) if r < d else 1
+            res = oracle.rect(ext, r, "sum", "f32_comp", "geometric", params=[float(q), m], lib=lib)
+            for o in range(O):
+                w1 = float(_geom_prefix((o + 1) * R, q, m) - _geom_prefix(o * R, q, m))
+                w2 = float(_geom_prefix((o + 1) * R, q * q, m) - _geom_prefix(o * R, q * q, m))
+                assert abs(res.abs_sum[o] - w1) <= 1e-14 * max(w1, 1e-300), ("geom abs_sum", ext, r, o)
+                assert abs(res.sq_sum[o] - w2) <= 1e-14 * max(w2, 1e-300), ("geom sq_sum", ext, r, o)
+
+
+def pin_conditioning_library(lib):
+    """sum|t| and sum t^2 against numpy reductions of the FP64 body values (each
+    t = A x w is exact in FP64), for every oracle entry that returns them:
+    rect, rect_flat and rect_sampled (LOAD and DOT_BCAST, sum and max), and the
+    CSR rows against scipy-built per-row values.  A sequential FP64 sum of n
+    non-negative terms errs by at most (n-1) u64 relative."""
+    g = np.random.Generator(np.random.PCG64(107))
+    u = 2.0 ** -53
+    for ext, r in (((6, 5, 33), 1), ((4, 3, 7, 9), 2), ((2, 300), 1), ((513,), 0), ((3, 4, 5), 3)):
+        d = len(ext)
+        O = int(np.prod(ext[:r])) if r else 1
+        R = int(np.prod(ext[r:])) if r < d else 1
+        A = (g.standard_normal(int(np.prod(ext))) * np.exp2(g.integers(-8, 9, int(np.prod(ext))))).astype(np.float32)
+        w = g.uniform(-3, 3, R).astype(np.float32)
+        for body in ("load", "dot_bcast"):
+            T = A.astype(np.float64).reshape(O, R)
+            if body == "dot_bcast":
+                T = T * w.astype(np.float64)[None, :]
+            want1 = np.abs(T).sum(axis=1)
+            want2 = (T * T).sum(axis=1)
+            tol = (R + 2) * u
+            for op in ("sum", "max"):
+                for res in (oracle.rect(ext, r, op, "f32", body, A=A, w=w, lib=lib),
+                            oracle.rect_flat(ext, r, op, "f32", body, A=A, w=w, lib=lib)):
+                    assert np.all(np.abs(res.abs_sum - want1) <= tol * want1), ("abs_sum", ext, r, body, op)
+                    assert np.all(np.abs(res.sq_sum - want2) <= tol * want2), ("sq_sum", ext, r, body, op)
+                idx = g.integers(0, O, min(O, 7))
+                res = oracle.rect_sampled(ext, r, op, "f32", body, idx, A=A, w=w, lib=lib)
+                assert np.all(np.abs(res.abs_sum - want1[idx]) <= tol * want1[idx]), ("sampled abs_sum", ext, r)
+                assert np.all(np.abs(res.sq_sum - want2[idx]) <= tol * want2[idx]), ("sampled sq_sum", ext, r)
+    # CSR rows: per-row |val x| and (val x)^2 summed by numpy
+    n_rows, n_cols = 400, 500
+    lens = np.minimum(g.zipf(1.5, n_rows), 200)
+    lens[::37] = 0
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    nnz = int(off[-1])
+    col = g.integers(0, n_cols, nnz).astype(np.int32)
+    val = g.standard_normal(nnz).astype(np.float32)
+    x = g.standard_normal(n_cols).astype(np.float32)
+    t = val.astype(np.float64) * x.astype(np.float64)[col]
+    want1 = np.array([np.abs(t[off[i]:off[i + 1]]).sum() for i in range(n_rows)])
+    want2 = np.array([(t[off[i]:off[i + 1]] ** 2).sum() for i in range(n_rows)])
+    for op in ("sum", "max"):
+        res = oracle.csr(off, col, val, x, op=op, lib=lib)
+        assert np.all(np.abs(res.abs_sum - want1) <= 202 * u * want1), ("csr abs_sum", op)
+        assert np.all(np.abs(res.sq_sum - want2) <= 202 * u * want2), ("csr sq_sum", op)
+        assert np.all(res.abs_sum[lens == 0] == 0) and np.all(res.sq_sum[lens == 0] == 0)
+    rows = g.integers(0, n_rows, 40)
+    res = oracle.csr(off, col, val, x, rows=rows, lib=lib)
+    assert np.array_equal(res.abs_sum, oracle.csr(off, col, val, x, lib=lib).abs_sum[rows]), "csr rows abs_sum"
+
+
+def pin_conditioning_brute(lib):
+    """sum|t| and sum t^2 against the pure-Python formulation (exactly rounded
+    sums) on every nest of depth <= 3 with extents <= 3."""
+    g = np.random.Generator(np.random.PCG64(108))
+    for d in (1, 2, 3):
+        for ext in itertools.product(range(4), repeat=d):
+            total = int(np.prod(ext))
+            A = g.standard_normal(max(total, 1)).astype(np.float32)
+            for r in range(d + 1):
+                R = int(np.prod(ext[r:])) if r < d else 1
+                w = g.uniform(-2, 2, max(R, 1)).astype(np.float32)
+                want1, want2 = brute.rect_conditioning(ext, r, "dot_bcast", A=A, w=w)
+                for fn in (oracle.rect, oracle.rect_flat):
+                    res = fn(ext, r, "sum", "f32", "dot_bcast", A=A, w=w, lib=lib)
+                    assert len(res.abs_sum) == len(want1)
+                    for got, want in ((res.abs_sum, want1), (res.sq_sum, want2)):
+                        assert all(abs(gv - wv) <= 32 * 2.0 ** -53 * wv for gv, wv in zip(got, want)), \
+                            ("brute conditioning", ext, r, fn.__name__)
+
+
 ALL_PINS = [
     pin_affine_sum_every_level,
     pin_affine_max_min_every_level,
@@ -318,4 +439,7 @@ ALL_PINS = [
     pin_brute_force_tiny,
     pin_formulations_agree,
     pin_paper_examples,
+    pin_conditioning_closed_forms,
+    pin_conditioning_library,
+    pin_conditioning_brute,
 ]

@@ -4,7 +4,9 @@ Each case builds the oracle C file with one planted mistake (a compile-time
 switch that is 0 in every other build) into a temporary library and runs the
 full pin battery against it.  A pin battery that let a dropped term, a flipped
 sign, a transposed operand, a lost compensation or a wrong reduction level
-through would not pin the oracle.  CPU only.
+through would not pin the oracle; nor would one that let an inflated or
+misformed conditioning sum (sum|t|, sum t^2: the scales of every FP tolerance)
+through.  CPU only.
 """
 import os
 
@@ -19,6 +21,9 @@ MUTATIONS = {
     3: "transposes the broadcast operand's two innermost indices",
     4: "drops the Neumaier compensation",
     5: "reduces one level too few",
+    6: "doubles sum|t|",
+    7: "adds |t| to sum t^2",
+    8: "drops the absolute value in sum|t|",
 }
 
 
