@@ -361,8 +361,12 @@ void hp_nest_destroy(hp_nest *n);
  * streams the scheduler launches steps on.  Needs a GPU (HP_ECUDA otherwise). */
 hp_status hp_serve_create(size_t mem_budget_bytes, int max_slots, int n_streams, hp_server **out);
 
-/* Submit one request: a nest (shape and plan; must stay alive until polled
- * done), its device inputs and output.  Returns a ticket. */
+/* Submit one request: a nest (shape and plan), its device inputs and output.
+ * Returns a ticket.  The server prepares the nest's device state and its
+ * launch configuration on first use, from the scheduler thread, so from
+ * submission until every ticket on it is polled done the caller must not run,
+ * tune or destroy that nest (hp_nest_run*, hp_nest_tune*, hp_nest_destroy):
+ * those calls would race with the scheduler on the nest's state. */
 hp_status hp_serve_submit(hp_server *s, const hp_nest *shape, const void *const *in_dev, void *out_dev,
                           uint64_t *ticket);
 

@@ -28,6 +28,10 @@ hp_status ensure_device(hp_nest* n) {
     if (dev != n->device) return fail(HP_EINVAL, "nest was first run on another device");
     return HP_OK;
   }
+  // hp_nest_run_static sizes the launch (and sets the kernels' attributes) on
+  // its own device without taking the nest's device: that launch
+  // configuration belongs to that device
+  if (n->cfg.ready && n->cfg.device != dev) return fail(HP_EINVAL, "nest was first run on another device");
   int sms = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return cuda_fail(e, "device query");

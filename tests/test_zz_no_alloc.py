@@ -23,10 +23,17 @@ CASES = [
     ([5, 3, 10000], 1, "sum", "i64", "dot_bcast", ["grid", ("grid", 0, 1), "warp"]),
     ([4, 9, 700], 1, "max", "i32", "load", ["grid", ("grid", 0, 2), "cta"]),
     ([3, 200000], 1, "sum", "f32_comp", "load", None),
+    # cluster teams (DSMEM) over grid parts: the launch sets the cluster
+    # attributes on first use, here first through the static entry point
+    ([3, 8, 16, 1024], 1, "sum", "f32_comp", "dot_bcast", ["grid", ("grid", 0, 4), ("cluster", 4, 0), ("cta", 4, 0)]),
+    ([3, 4, 16, 512], 1, "sum", "f32", "dot_bcast", ["grid", ("grid", 0, 2), ("cluster", 16, 0), ("cta", 2, 0)]),
 ]
 
+# expected plan fields per case (None = any): cluster size and grid parts
+PLAN_FIELDS = {5: {"cluster": 4, "grid_parts": 2}, 6: {"cluster": 16, "grid_parts": 2}}
 
-def _run(case, seed):
+
+def _inputs(case, seed):
     import torch
     ext, r, op, prec, body, lm = case
     g = np.random.Generator(np.random.PCG64(seed))
@@ -40,6 +47,13 @@ def _run(case, seed):
         A = torch.from_numpy(g.standard_normal(total).astype(np.float32)).cuda()
         w = torch.from_numpy(g.uniform(-1, 1, R).astype(np.float32)).cuda()
         dt = torch.float32
+    return (A, w), dt
+
+
+def _run(case, seed):
+    import torch
+    ext, r, op, prec, body, lm = case
+    (A, w), dt = _inputs(case, seed)
     ins = [A.data_ptr()] + ([w.data_ptr()] if body == "dot_bcast" else [])
     O = int(np.prod(ext[:r]))
     stream = torch.cuda.current_stream().cuda_stream
@@ -61,8 +75,16 @@ def _run(case, seed):
     return ref, got
 
 
-@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}-{c[2]}-{c[3]}")
-def test_static_scratch_matches_allocating_entry_point(case):
+@pytest.mark.parametrize("idx", range(len(CASES)), ids=lambda i: f"{CASES[i][0]}-{CASES[i][2]}-{CASES[i][3]}")
+def test_static_scratch_matches_allocating_entry_point(idx):
+    case = CASES[idx]
+    want = PLAN_FIELDS.get(idx, {})
+    if want:
+        ext, r, op, prec, body, lm = case
+        n = hb.Nest(ext, r, op, prec, body, level_map=lm)
+        d = n.describe()
+        n.close()
+        assert {k: d[k] for k in want} == want, d
     ref, got = _run(case, seed=11)
     for g in got:
         # same kernels and reduction tree: identical bits (the tolerance the
@@ -78,3 +100,24 @@ def test_static_scratch_rejects_plans_beyond_its_size():
         n.run_static([0x1000], 0x1000, 0)
     assert e.value.status == hb.HP_EINVAL and "static maximum" in str(e.value)
     n.close()
+
+
+def test_static_then_allocating_run_on_one_nest():
+    """One nest run first without allocating, then through hp_nest_run: the
+    launch configuration the static call sized is reused and the bits agree."""
+    import torch
+    case = CASES[5]
+    ext, r, op, prec, body, lm = case
+    (A, w), dt = _inputs(case, seed=12)
+    ins = [A.data_ptr(), w.data_ptr()]
+    O = int(np.prod(ext[:r]))
+    stream = torch.cuda.current_stream().cuda_stream
+    n = hb.Nest(ext, r, op, prec, body, level_map=lm)
+    outs = []
+    for runner in (n.run_static, n.run, n.run_static):
+        out = torch.full((O,), 7, dtype=dt, device="cuda")
+        runner(ins, out.data_ptr(), stream)
+        torch.cuda.synchronize()
+        outs.append(out.cpu().numpy())
+    n.close()
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
