@@ -8,7 +8,11 @@ CTAs of a cluster (distributed shared memory), each CTA folding 4 of the 16 j
 rows.  Compensated FP32 accumulation.
 
 One step = one run of the nest (all its launches) over the resident inputs.
-Metric: nest iterations per second (2^29 iterations per step).
+Metric: nest iterations per second (2^29 iterations per step).  The line also
+carries the per-result error of every output the CPU-baseline leg evaluated
+against the FP64 oracle (`parity`), and, after the headline's timed region,
+the GEMV-shaped nest, the 10,000-nest batch and 10 s of Poisson serving
+(`workloads`; --extras none leaves them out).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hp|reference]
 
@@ -76,6 +80,92 @@ def measured_peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def host_cores():
+    """Host cores this process may run on (affinity) and online in the machine."""
+    try:
+        aff = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        aff = os.cpu_count() or 1
+    return {"affinity": aff, "online": os.cpu_count() or aff}
+
+
+def threaded(fn, items, threads):
+    """fn over items on `threads` host threads, results in order.  The oracle's
+    C entry points run outside the interpreter lock (ctypes releases it), so
+    its calls on disjoint outputs run in parallel."""
+    from concurrent.futures import ThreadPoolExecutor
+    if threads <= 1:
+        return [fn(x) for x in items]
+    with ThreadPoolExecutor(threads) as ex:
+        return list(ex.map(fn, items))
+
+
+def fp_parity(got, ref, prec, bound, tol):
+    """Per-result error of GPU FP32 sums against the FP64 oracle, summarised.
+
+    For each result: err = |got - ref|; the relative error err / |ref| where
+    |ref| >= 2^-20 sum|t| (the relative clause), else the normalized error
+    err / (2^-20 sum|t|) (cond = sum|t| / |ref| above 2^20); the plain relative
+    error err / |ref| of every nonzero ref; cond = sum|t| / |ref|; and the
+    a-priori bound check err <= bound sum|t| + 2^-24 |ref|.  Plain FP32 sums
+    are also scaled by sqrt(sum t^2) (a random-sign sum's natural scale)."""
+    g = np.asarray(got, np.float64)
+    r, ab, sq = ref.values, ref.abs_sum, ref.sq_sum
+    err = np.abs(g - r)
+    floor = 2.0 ** -20 * ab
+    rel_clause = np.abs(r) >= floor
+    scale = np.maximum(np.abs(r), floor)
+    safe = np.where(scale > 0, scale, 1.0)
+    norm = np.where(scale > 0, err / safe, np.where(err > 0, np.inf, 0.0))
+    nz = r != 0
+    rel = err[nz] / np.abs(r[nz])
+    cond = np.where(nz, ab / np.where(nz, np.abs(r), 1.0), np.inf)
+    lim = bound * ab + 2.0 ** -24 * np.abs(r)
+    worst = int(np.argmax(norm)) if norm.size else 0
+    d = {
+        "n_checked": int(g.size), "prec": prec, "tolerance": tol,
+        "clause": "|got-ref| / max(|ref|, 2^-20 sum|t|)",
+        "n_relative_clause": int(rel_clause.sum()), "n_normalized_clause": int((~rel_clause).sum()),
+        "max_norm_err": float(norm.max()) if norm.size else 0.0,
+        "p50_norm_err": float(np.median(norm)) if norm.size else 0.0,
+        "p99_norm_err": float(np.quantile(norm, 0.99)) if norm.size else 0.0,
+        "worst": {"index": worst, "got": float(g[worst]), "ref": float(r[worst]), "sum_abs": float(ab[worst]),
+                  "cond": float(cond[worst])} if norm.size else None,
+        "max_plain_rel_err": float(rel.max()) if rel.size else 0.0,
+        "max_cond": float(cond[np.isfinite(cond)].max()) if np.isfinite(cond).any() else None,
+        "median_cond": float(np.median(cond)) if cond.size else None,
+        "n_exact_zero_ref": int((~nz).sum()),
+        "a_priori_bound": bound, "max_err_over_sum_abs": float((err / np.where(ab > 0, ab, 1.0)).max()) if err.size else 0.0,
+        "within_a_priori_bound": bool(np.all(err <= lim * (1 + 1e-12) + 1e-300)),
+    }
+    if prec == "f32":
+        l2 = np.sqrt(sq)
+        s2 = np.maximum(np.abs(r), l2)
+        n2 = np.where(s2 > 0, err / np.where(s2 > 0, s2, 1.0), 0.0)
+        d["max_norm_err_l2_scale"] = float(n2.max()) if n2.size else 0.0
+        d["pass"] = bool(d["max_norm_err_l2_scale"] <= tol and d["within_a_priori_bound"])
+        d["pass_sum_abs_clause"] = bool(d["max_norm_err"] <= tol)
+    else:
+        d["pass"] = bool(d["max_norm_err"] <= tol and d["within_a_priori_bound"])
+    return d
+
+
+def write_parity_table(path, idx, got, ref):
+    """Per-result error table (one line per checked output) for --parity-out."""
+    g = np.asarray(got, np.float64)
+    r = ref.values
+    with open(path, "w") as f:
+        f.write("output,got,ref_fp64,sum_abs,cond,abs_err,rel_err,norm_err,clause\n")
+        for k in range(g.size):
+            e = abs(g[k] - r[k])
+            fl = 2.0 ** -20 * ref.abs_sum[k]
+            clause = "relative" if abs(r[k]) >= fl else "normalized"
+            sc = max(abs(r[k]), fl)
+            f.write(f"{int(idx[k])},{g[k]!r},{r[k]!r},{ref.abs_sum[k]!r},"
+                    f"{(ref.abs_sum[k] / abs(r[k])) if r[k] else float('inf')!r},{e!r},"
+                    f"{(e / abs(r[k])) if r[k] else float('inf')!r},{(e / sc) if sc else 0.0!r},{clause}\n")
 
 
 def dist_env():
@@ -192,12 +282,14 @@ def run_hp(args):
 
     # plain FP32 variant (context), then the headline compensated run with clock sampling
     plain_ms, plain_per = timed(nests["f32"], max(3, args.steps), args.warmup)
+    got_plain = out.cpu().numpy().copy()
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
     total_ms, per = timed(nests["f32_comp"], args.steps, args.warmup)
     clocks = sampler.stop()
     assert nests["f32_comp"].check(sp) == 0
+    got_comp = out.cpu().numpy().copy()
 
     max_ms = replicas.max_over_ranks(total_ms, device="cuda")   # the slowest replica times the job
 
@@ -216,9 +308,22 @@ def run_hp(args):
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_s = replicas.max_over_ranks(e2e_s, device="cuda")
 
-    cpu = None
+    cpu, parity = None, None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(A, w, seconds=args.cpu_seconds)
+        cpu, sel, ref = cpu_baseline(A, w, seconds=args.cpu_seconds)
+        # the oracle's outputs of the CPU-baseline leg are the parity reference:
+        # every output it evaluated, compensated and plain FP32 against FP64
+        parity = {"f32_comp": fp_parity(got_comp[sel], ref, "f32_comp", nests["f32_comp"].error_bound(), 1e-6),
+                  "f32": fp_parity(got_plain[sel], ref, "f32", nests["f32"].error_bound(), 1e-5),
+                  "oracle": "FP64 Neumaier sums of the FP64 products (exact) in loop order"}
+        if args.parity_out:
+            write_parity_table(args.parity_out, sel, got_comp[sel], ref)
+    workloads = {}
+    if rank == 0:
+        for name in [x for x in args.extras.split(",") if x and x != "none"]:
+            t_w = time.perf_counter()
+            workloads[name] = EXTRAS[name](args)
+            workloads[name]["wall_s"] = time.perf_counter() - t_w
 
     if rank == 0:
         peak, peak_kind = measured_peaks()
@@ -270,6 +375,9 @@ def run_hp(args):
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
             "cpu_baseline": cpu,
+            "parity": parity,
+            "host_cores": host_cores(),
+            "workloads": workloads,
         }
         print(json.dumps(line))
     for n in nests.values():
@@ -280,21 +388,40 @@ def run_hp(args):
 
 def cpu_baseline(A, w, seconds=15.0):
     """The oracle as it stands (sequential, one host core) on a bounded sample:
-    whole outputs of the same workload, as many as fit in about `seconds`."""
+    whole outputs of the same workload, as many as fit in about `seconds`.
+    Then, as context, the same outputs evaluated with the outermost level
+    spread over every host core (one oracle call per block of outputs).
+    Returns (baseline dict, evaluated output indices, oracle result)."""
     import oracle
     oracle.load()
     t0 = time.perf_counter()
     n_done = 0
     chunk = 256
     idx = np.arange(N_OUT, dtype=np.int64)
+    parts = []
     while n_done < N_OUT and time.perf_counter() - t0 < seconds:
         sel = idx[n_done:n_done + chunk]
-        oracle.rect_sampled(EXTENTS, RED_LEVEL, "sum", "f32_comp", "dot_bcast", sel, A=A, w=w)
+        parts.append(oracle.rect_sampled(EXTENTS, RED_LEVEL, "sum", "f32_comp", "dot_bcast", sel, A=A, w=w))
         n_done += sel.size
         chunk = min(chunk * 2, 4096)
     dt = time.perf_counter() - t0
-    return {"value": n_done * R / dt, "unit": "iterations/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n_done} of {N_OUT} outputs ({n_done * R} iterations) of the same workload, {dt:.1f} s"}
+    ref = oracle.Result(np.concatenate([p.values for p in parts]), np.concatenate([p.abs_sum for p in parts]),
+                        np.concatenate([p.sq_sum for p in parts]))
+    cores = host_cores()
+    threads = cores["affinity"]
+    blocks = np.array_split(idx[:n_done], max(1, threads * 4))
+    t1 = time.perf_counter()
+    par = threaded(lambda b: oracle.rect_sampled(EXTENTS, RED_LEVEL, "sum", "f32_comp", "dot_bcast", b, A=A, w=w),
+                   blocks, threads)
+    dt_all = time.perf_counter() - t1
+    same = bool(np.array_equal(np.concatenate([p.values for p in par]), ref.values))
+    return ({"value": n_done * R / dt, "unit": "iterations/s", "cores": 1, "kind": "oracle",
+             "sample": f"{n_done} of {N_OUT} outputs ({n_done * R} iterations) of the same workload, {dt:.1f} s",
+             "host_cores": cores,
+             "all_cores_context": {"value": n_done * R / dt_all, "unit": "iterations/s", "cores": threads,
+                                   "seconds": dt_all, "same_values": same,
+                                   "how": "the same oracle calls, outermost level split over host threads"}},
+            idx[:n_done], ref)
 
 
 def run_reference(args):
@@ -333,7 +460,8 @@ def run_reference(args):
         "dtype": "f64",
         "data": "synthetic (seeded): A normal(0,1) seed 3, w uniform[-1,1] seed 4",
         "config": {"workload": WORKLOAD, "l2": "host run"},
-        "cpu_baseline": {"value": value, "unit": "iterations/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "iterations/s", "cores": 1, "kind": "oracle", "sample": sample,
+                         "host_cores": host_cores()},
         "e2e": {"value": value, "unit": "iterations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -427,30 +555,68 @@ def run_csr_workload(args):
     n.close()
 
 
-def run_gemv_workload(args):
-    """2-level nest 1024 x 1024 (GEMV-shaped), FP32 and int32, one launch; L2 flushed
-    between timed launches (a 256 MiB write) and also timed warm."""
+def gemv_measure(args):
+    """2-level nest 1024 x 1024 (GEMV-shaped), compensated FP32, plain FP32 and
+    int32, one launch per step; timed cold (L2 flushed between launches by a
+    256 MiB write), warm, and warm as a one-launch CUDA graph replay.  Its
+    CPU-baseline leg evaluates every output in the oracle; parity compares them
+    (FP within tolerance, int32 bit for bit)."""
     import torch
 
     from paper_2309_01906_gb300 import binding as hb
     from paper_2309_01906_gb300 import synth
     stream = torch.cuda.Stream()
     scrub = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
-    res = {}
+    peak, kind = measured_peaks()
+    alg = 4 * (1 << 20) + 2 * 4096
+    steps = max(args.steps, 20)
+    res, cpu = {}, None
     for prec, (A, x) in (("f32_comp", synth.gemv_f32()), ("f32", synth.gemv_f32()), ("i32", synth.gemv_i32())):
         dA = torch.from_numpy(A.reshape(-1)).cuda()
         dx = torch.from_numpy(x).cuda()
         out = torch.empty(1024, dtype=torch.int32 if prec == "i32" else torch.float32, device="cuda")
-        n = hb.Nest([1024, 1024], 1, "sum", prec, "dot_bcast", level_map=["grid", "warp"])
-        run = lambda: n.run([dA.data_ptr(), dx.data_ptr()], out.data_ptr(), stream.cuda_stream)  # noqa: E731
-        cold = _event_time(run, args.steps, args.warmup, stream, flush=lambda: scrub.fill_(1.0))
-        warm = _event_time(run, args.steps, args.warmup, stream)
-        res[prec] = {"cold_us": cold * 1e3, "warm_us": warm * 1e3,
-                     "iterations_per_s_cold": (1 << 20) / (cold * 1e-3)}
+        n = hb.Nest([1024, 1024], 1, "sum", prec, "dot_bcast", level_map=args.gemv_map)
+        run = hb.PreparedRun(n.handle, [dA.data_ptr(), dx.data_ptr()], out.data_ptr())
+        sp = stream.cuda_stream
+        cold = _event_time(lambda: run(sp), steps, args.warmup, stream, flush=lambda: scrub.fill_(1.0))
+        warm = _event_time(lambda: run(sp), steps, args.warmup, stream)
+        # the same launch captured once in a CUDA graph and replayed
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            run(torch.cuda.current_stream().cuda_stream)
+        warm_graph = _event_time(g.replay, steps, args.warmup, stream)
+        cold_graph = _event_time(g.replay, steps, args.warmup, stream, flush=lambda: scrub.fill_(1.0))
+        got = out.cpu().numpy()
+        plan = n.describe()
+        # CPU-baseline leg: the oracle on all 1024 outputs, timed; its outputs are the parity reference
+        import oracle
+        t0 = time.perf_counter()
+        ref = oracle.rect([1024, 1024], 1, "sum", prec, "dot_bcast", A=A, w=x)
+        dt = time.perf_counter() - t0
+        if prec == "i32":
+            par = {"n_checked": 1024, "bit_exact": bool(np.array_equal(got.astype(np.int64), ref.values))}
+        else:
+            par = fp_parity(got, ref, prec, n.error_bound(), 1e-6 if prec == "f32_comp" else 1e-5)
+        if prec == "f32_comp":
+            cpu = {"value": (1 << 20) / dt, "unit": "iterations/s", "cores": 1, "kind": "oracle",
+                   "sample": "all 1024 outputs of the compensated FP32 nest"}
+        res[prec] = {"cold_us": cold * 1e3, "warm_us": warm * 1e3, "graph_warm_us": warm_graph * 1e3,
+                     "graph_cold_us": cold_graph * 1e3,
+                     "iterations_per_s_cold": (1 << 20) / (cold * 1e-3),
+                     "roofline_cold": {"bound": "hbm", "achieved": alg / (cold * 1e-3) / 1e9, "peak": peak,
+                                       "unit": "GB/s", "frac": alg / (cold * 1e-3) / 1e9 / peak, "peak_kind": kind},
+                     "plan": {k: plan[k] for k in ("team", "warps", "team_lanes", "vec", "grid_parts", "kernel")},
+                     "parity": par}
+        del g
         n.close()
-    print(json.dumps({"workload": "2-level nest 1024 x 1024, out[i] = sum_j A[i][j] * x[j], one launch",
-                      "map": "i -> grid, j -> warp (lanes x 4 vector slots)", "results": res,
-                      "algorithmic_bytes": 4 * (1 << 20) + 2 * 4096}))
+    return {"workload": "2-level nest 1024 x 1024, out[i] = sum_j A[i][j] * x[j], one launch (FP32 uniform[-1,1] "
+                        "seed 1; int32 uniform [-100,100] seed 2)",
+            "map": str(args.gemv_map), "results": res, "algorithmic_bytes": alg, "cpu_baseline": cpu,
+            "steps": steps, "l2": "cold: 256 MiB write between launches; warm: inputs resident in L2"}
+
+
+def run_gemv_workload(args):
+    print(json.dumps(gemv_measure(args)))
 
 
 # FP32 FMA peak derived from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
@@ -684,9 +850,50 @@ def _plan_class(d):
         ("/split" if d["grid_parts"] > 1 else "")
 
 
-def run_batch_workload(args):
+def batch_parity(wl, idxs, threads):
+    """CPU-baseline leg of the batched workload: the oracle evaluates the listed
+    nests (all their outputs) on `threads` host threads; the batched outputs are
+    compared with it (FP32 compensated sums within 1e-6 of the normalized
+    error, int32 max bit for bit).  Returns (parity dict, oracle seconds)."""
+    import oracle
+    import torch
+    from paper_2309_01906_gb300 import synth
+
+    def one(i):
+        sh = wl["shapes"][i]
+        A = synth.nest_input(sh, i, 9)
+        return oracle.rect(list(sh.extents), sh.red_level, sh.op, sh.prec, "load", A=A)
+
+    t0 = time.perf_counter()
+    refs = threaded(one, idxs, threads)
+    dt = time.perf_counter() - t0
+    worst, n_fp, n_int, int_ok, bound_ok, n_out = 0.0, 0, 0, True, True, 0
+    for i, ref in zip(idxs, refs):
+        sh = wl["shapes"][i]
+        k, _, oo = wl["place"][i]
+        got = wl["dev_out"][k][oo:oo + sh.n_out].cpu().numpy() if sh.n_out else np.zeros(0)
+        n_out += sh.n_out
+        if sh.op == "sum":
+            n_fp += 1
+            p = fp_parity(got, ref, "f32_comp", wl["nests"][i].error_bound(), 1e-6)
+            worst = max(worst, p["max_norm_err"])
+            bound_ok &= p["within_a_priori_bound"]
+        else:
+            n_int += 1
+            int_ok &= bool(np.array_equal(got.astype(np.int64), ref.values))
+    torch.cuda.synchronize()
+    return ({"nests_checked": len(idxs), "outputs_checked": n_out, "fp32_comp_sum_nests": n_fp,
+             "int32_max_nests": n_int, "max_norm_err": worst, "tolerance": 1e-6,
+             "within_a_priori_bound": bool(bound_ok), "int32_bit_exact": bool(int_ok),
+             "pass": bool(worst <= 1e-6 and bound_ok and int_ok),
+             "sample": f"{len(idxs)} nests drawn with seed 19 from the same 10,000 (sigma 2, T up to 2^24)"}, dt)
+
+
+def batch_measure(args):
     """Batched uneven nests: one persistent launch per arithmetic under a CUDA graph
-    vs one hp_nest_run per nest (same plans, same stream, no graph)."""
+    vs one hp_nest_run per nest (same plans, same stream, no graph).  Batched
+    outputs must equal the per-nest ones bit for bit; a seeded sample of nests
+    is checked against the oracle."""
     import torch
 
     from paper_2309_01906_gb300 import binding as hb
@@ -702,7 +909,7 @@ def run_batch_workload(args):
         for i, nest in enumerate(wl["nests"]):
             if i not in set(keep):
                 nest.close()
-        for k in ("shapes", "nests", "ins", "outs"):
+        for k in ("shapes", "nests", "ins", "outs", "place"):
             wl[k] = [wl[k][i] for i in keep]
         wl["bytes"] = int(sum(sh.size for sh in wl["shapes"])) * 4
         wl["iters"] = int(sum(sh.size for sh in wl["shapes"]))
@@ -733,7 +940,8 @@ def run_batch_workload(args):
             ms = _event_time(lambda: hb.hp_nest_run_batch(pb, stream=sp), steps, args.warmup, stream)
             nbytes = sum(wl["shapes"][i].size for i in idxs) * 4
             breakdown[key] = {"nests": len(idxs), "bytes": nbytes, "ms": ms, "gbs": nbytes / (ms * 1e-3) / 1e9}
-    ms_plain = _event_time(plain, steps, args.warmup, stream)
+    plain_steps = max(1, min(steps, args.batch_plain_steps))
+    ms_plain = _event_time(plain, plain_steps, min(args.warmup, 3), stream)
     ref = {k: v.clone() for k, v in wl["dev_out"].items()}
     ms_batch = _event_time(batched, steps, args.warmup, stream)
     same = all(torch.equal(ref[k], wl["dev_out"][k]) for k in ref)
@@ -743,41 +951,77 @@ def run_batch_workload(args):
     for nest in wl["nests"]:
         key = _plan_class(nest.describe())
         teams[key] = teams.get(key, 0) + 1
-    print(json.dumps({
+    parity, cpu = None, None
+    if args.batch_check > 0 and not args.no_cpu_baseline:
+        g = np.random.Generator(np.random.PCG64(19))
+        idxs = sorted(int(i) for i in g.choice(n, size=min(n, args.batch_check), replace=False))
+        threads = host_cores()["affinity"]
+        parity, dt = batch_parity(wl, idxs, threads)
+        it = int(sum(wl["shapes"][i].size for i in idxs))
+        cpu = {"value": len(idxs) / dt, "unit": "nests/s", "iterations_per_s": it / dt, "cores": threads,
+               "kind": "oracle", "sample": f"{len(idxs)} of the {n} nests ({it} iterations), whole nests"}
+    gbs = wl["bytes"] / (ms_batch * 1e-3) / 1e9
+    res = {
         "workload": f"{n} uneven nests (depth 2-5, lognormal sizes), FP32 compensated sums and int32 max",
-        "iterations": wl["iters"], "input_bytes": wl["bytes"],
-        "batched": {"ms": ms_batch, "nests_per_s": n / (ms_batch * 1e-3), "iterations_per_s": wl["iters"] / (ms_batch * 1e-3),
-                    "achieved_gbs": wl["bytes"] / (ms_batch * 1e-3) / 1e9, "frac": wl["bytes"] / (ms_batch * 1e-3) / 1e9 / peak},
+        "metric": "nests/s", "iterations": wl["iters"], "input_bytes": wl["bytes"],
+        "batched": {"ms": ms_batch, "nests_per_s": n / (ms_batch * 1e-3),
+                    "iterations_per_s": wl["iters"] / (ms_batch * 1e-3)},
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                     "peak_kind": kind, "algorithmic_bytes": wl["bytes"], "kernel": "batch_kernel"},
         "plain_one_launch_per_nest": {"ms": ms_plain, "nests_per_s": n / (ms_plain * 1e-3),
-                                      "achieved_gbs": wl["bytes"] / (ms_plain * 1e-3) / 1e9},
-        "speedup": ms_plain / ms_batch, "bit_identical": bool(same), "peak_gbs": peak, "peak_kind": kind,
+                                      "achieved_gbs": wl["bytes"] / (ms_plain * 1e-3) / 1e9, "steps": plain_steps},
+        "speedup": ms_plain / ms_batch, "bit_identical_to_per_nest_runs": bool(same),
         "plans": teams, "breakdown": breakdown, "tuned_classes": wl["tuned_classes"], "setup_s": setup_s,
-        "steps": steps, "warmup": args.warmup}))
+        "parity": parity, "cpu_baseline": cpu, "steps": steps, "warmup": args.warmup,
+        "l2": "inputs (16 GB) larger than L2; no flush"}
     for nest in wl["nests"]:
         nest.close()
+    return res
 
 
-def run_serve_workload(args):
+def run_batch_workload(args):
+    print(json.dumps(batch_measure(args)))
+
+
+def serve_measure(args):
     """Serving: a Poisson stream of nest requests (seed 10) at --serve-rate for
     --serve-seconds; shapes drawn as in the batched workload (seed 9), all FP32
     compensated sums over pre-generated device inputs; 40 GiB admission budget.
     The same arrival sequence is served by the batched server and by the plain
-    per-request server; latency is submission to observed completion."""
+    per-request server.  Latency runs from each request's scheduled arrival to
+    the server observing its completion (hp_serve_submit_at), so a client that
+    falls behind its schedule counts its lag.  A seeded 1% of the requests
+    write to outputs of their own; each is compared bit for bit with a single
+    hp_nest_run of its nest and, in the CPU-baseline leg, with the oracle."""
     import torch
 
     from paper_2309_01906_gb300 import binding as hb
     from paper_2309_01906_gb300 import synth
     n_pool = args.serve_pool
     shapes = synth.uneven_shapes(n_nests=n_pool, seed=9, sum_prec="f32_comp")
+    t_setup = time.perf_counter()
+    hosts = threaded(lambda i: synth.normal_f32(shapes[i].size, 9, 1 + i), range(n_pool), 4)
     pool = []
     for i, sh in enumerate(shapes):
-        A = synth.normal_f32(sh.size, 9, 1 + i)
         n = hb.Nest(list(sh.extents), sh.red_level, "sum", "f32_comp", "load")
         outs = [torch.empty(max(sh.n_out, 1), dtype=torch.float32, device="cuda") for _ in range(4)]
-        pool.append((n, torch.from_numpy(A).cuda(), outs, sh))
+        pool.append((n, torch.from_numpy(hosts[i]).cuda(), outs, sh))
     arrivals = synth.poisson_arrivals(rate=args.serve_rate, duration=args.serve_seconds, seed=10)
     pick = np.random.Generator(np.random.PCG64(np.random.SeedSequence(10, spawn_key=(1,)))).integers(
         0, n_pool, arrivals.size)
+    g_s = np.random.Generator(np.random.PCG64(np.random.SeedSequence(10, spawn_key=(2,))))
+    sampled = np.sort(g_s.choice(arrivals.size, size=max(1, int(arrivals.size * args.serve_check)), replace=False))
+    sampled_set = set(int(j) for j in sampled)
+    # single-run results of every sampled nest (the same plan: the served bits must equal them)
+    stream = torch.cuda.current_stream().cuda_stream
+    single = {}
+    for k in sorted(set(int(pick[j]) for j in sampled)):
+        n, dA, _, sh = pool[k]
+        o = torch.empty(max(sh.n_out, 1), dtype=torch.float32, device="cuda")
+        n.run([dA.data_ptr()], o.data_ptr(), stream)
+        single[k] = o
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup
     iters = float(np.mean([pool[k][3].size for k in pick]))
 
     def serve(batching):
@@ -787,19 +1031,29 @@ def run_serve_workload(args):
         finally:
             hb.hp_set_option("serve_batching", 1)
         use = [0] * n_pool
-        lag = 0.0
-        t0 = time.perf_counter()
+        lags = np.zeros(arrivals.size)
+        own = {}
+        for j in sampled:
+            sh = pool[int(pick[j])][3]
+            own[int(j)] = torch.full((max(sh.n_out, 1),), float("nan"), dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        clock = hb.hp_serve_clock_us
+        t0 = clock()
         last = 0
         for j, t_arr in enumerate(arrivals):
+            due = t0 + t_arr * 1e6
             while True:
-                now = time.perf_counter() - t0
-                if now >= t_arr:
+                now = clock()
+                if now >= due:
                     break
-            lag = max(lag, now - t_arr)
+            lags[j] = now - due
             n, dA, outs, _ = pool[pick[j]]
-            out = outs[use[pick[j]] % 4]
-            use[pick[j]] += 1
-            last = hb.hp_serve_submit(server, n.handle, [dA.data_ptr()], out.data_ptr())
+            if j in sampled_set:
+                out = own[j]
+            else:
+                out = outs[use[pick[j]] % 4]
+                use[pick[j]] += 1
+            last = hb.hp_serve_submit_at(server, n.handle, [dA.data_ptr()], out.data_ptr(), due)
         hb.hp_serve_poll(server, last, -1)
         deadline = time.perf_counter() + 120
         while hb.hp_serve_counters(server)["completed"] < arrivals.size and time.perf_counter() < deadline:
@@ -807,20 +1061,60 @@ def run_serve_workload(args):
         st = hb.hp_serve_stats(server)
         c = hb.hp_serve_counters(server)
         hb.hp_serve_destroy(server)
+        torch.cuda.synchronize()
+        same = all(torch.equal(own[int(j)], single[int(pick[j])]) for j in sampled)
         st.update({"completed": c["completed"], "steps": c["steps"], "peak_bytes": c["peak_bytes"],
-                   "peak_slots": c["peak_slots"], "max_submit_lag_ms": lag * 1e3})
-        return st
+                   "peak_slots": c["peak_slots"], "submit_lag_us_p50": float(np.median(lags)),
+                   "submit_lag_us_p99": float(np.quantile(lags, 0.99)), "submit_lag_us_max": float(lags.max()),
+                   "sampled_bit_identical_to_single_runs": bool(same)})
+        return st, own
 
-    batched = serve(True)
-    plain = serve(False)
-    print(json.dumps({
+    batched, own_b = serve(True)
+    plain, _ = serve(False)
+    # CPU-baseline leg: the oracle on every distinct sampled nest; the served outputs against it
+    parity, cpu = None, None
+    if not args.no_cpu_baseline:
+        import oracle
+        ks = sorted(single)
+        threads = host_cores()["affinity"]
+        t1 = time.perf_counter()
+        refs = dict(zip(ks, threaded(lambda k: oracle.rect(list(pool[k][3].extents), pool[k][3].red_level, "sum",
+                                                           "f32_comp", "load", A=hosts[k]), ks, threads)))
+        dt = time.perf_counter() - t1
+        worst, bound_ok = 0.0, True
+        for j in sampled:
+            k = int(pick[j])
+            sh = pool[k][3]
+            got = own_b[int(j)][:sh.n_out].cpu().numpy() if sh.n_out else np.zeros(0)
+            p = fp_parity(got, refs[k], "f32_comp", pool[k][0].error_bound(), 1e-6)
+            worst = max(worst, p["max_norm_err"])
+            bound_ok &= p["within_a_priori_bound"]
+        parity = {"requests_checked": int(sampled.size), "distinct_nests": len(ks), "max_norm_err": worst,
+                  "tolerance": 1e-6, "within_a_priori_bound": bool(bound_ok),
+                  "pass": bool(worst <= 1e-6 and bound_ok and batched["sampled_bit_identical_to_single_runs"]),
+                  "sample": f"seeded {100 * args.serve_check:.0f}% of the requests of the batched run"}
+        it = int(sum(pool[k][3].size for k in ks))
+        cpu = {"value": len(ks) / dt, "unit": "nests/s", "iterations_per_s": it / dt, "cores": threads,
+               "kind": "oracle", "sample": f"{len(ks)} distinct sampled nests ({it} iterations)"}
+    res = {
         "workload": f"Poisson {args.serve_rate:.0f} req/s for {args.serve_seconds:.0f} s, {arrivals.size} requests over "
                     f"{n_pool} pre-generated uneven nests (FP32 compensated sums), 40 GiB budget, 4 streams",
+        "metric": "latency from scheduled arrival (us) and nests/s",
         "mean_iterations_per_request": iters, "offered_gbs": args.serve_rate * iters * 4 / 1e9,
         "batched": batched, "plain_per_request": plain,
-        "p99_speedup": plain["p99_us"] / batched["p99_us"] if batched["p99_us"] else None}))
+        "p99_speedup": plain["p99_us"] / batched["p99_us"] if batched["p99_us"] else None,
+        "parity": parity, "cpu_baseline": cpu, "setup_s": setup_s}
     for n, _, _, _ in pool:
         n.close()
+    return res
+
+
+def run_serve_workload(args):
+    print(json.dumps(serve_measure(args)))
+
+
+EXTRAS = {"gemv": lambda a: gemv_measure(a), "batch": lambda a: batch_measure(a),
+          "serve": lambda a: serve_measure(a)}
 
 
 def main():
@@ -851,10 +1145,22 @@ def main():
     ap.add_argument("--batch-class", default="", help="batch: keep only the nests of this plan class (e.g. lanes/1)")
     ap.add_argument("--tune", action="store_true", help="batch: autotune one nest per shape class first")
     ap.add_argument("--serve-rate", type=float, default=20000.0)
-    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-seconds", type=float, default=None,
+                    help="serve: seconds of arrivals (60 for --workload serve, 10 inside the headline line)")
     ap.add_argument("--serve-pool", type=int, default=2000)
     ap.add_argument("--no-hist", action="store_true", help="csr: SpMV without the fused histogram")
+    ap.add_argument("--extras", default="gemv,batch,serve",
+                    help="nest4: other workloads measured after the headline and added to its line "
+                         "(comma list of gemv, batch, serve; 'none' for the headline alone)")
+    ap.add_argument("--parity-out", default="", help="nest4: write the per-result error table (CSV) here")
+    ap.add_argument("--batch-check", type=int, default=256, help="batch: nests compared with the oracle")
+    ap.add_argument("--batch-plain-steps", type=int, default=3, help="batch: timed passes of one launch per nest")
+    ap.add_argument("--serve-check", type=float, default=0.01, help="serve: fraction of requests checked")
+    ap.add_argument("--gemv-map", default="", help="gemv: level map, e.g. grid,warp (default: the planner's)")
     args = ap.parse_args()
+    args.gemv_map = [x.strip() for x in args.gemv_map.split(",")] if args.gemv_map else None
+    if args.serve_seconds is None:
+        args.serve_seconds = 60.0 if args.workload == "serve" else 10.0
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -370,12 +370,26 @@ hp_status hp_serve_create(size_t mem_budget_bytes, int max_slots, int n_streams,
 hp_status hp_serve_submit(hp_server *s, const hp_nest *shape, const void *const *in_dev, void *out_dev,
                           uint64_t *ticket);
 
+/* The serving clock: microseconds of the monotonic clock that the latency
+ * statistics use.  Host only; needs no GPU. */
+double hp_serve_clock_us(void);
+
+/* hp_serve_submit for a request whose arrival was scheduled at arrival_us (on
+ * the serving clock, not later than the call).  Its latency counts from
+ * arrival_us instead of from the call, so that a client that falls behind
+ * its arrival schedule does not hide the lag from the percentiles (open-loop
+ * load: latency from scheduled arrival to observed completion).  HP_EINVAL if
+ * arrival_us is negative or in the future. */
+hp_status hp_serve_submit_at(hp_server *s, const hp_nest *shape, const void *const *in_dev, void *out_dev,
+                             double arrival_us, uint64_t *ticket);
+
 /* HP_OK when the request finished (its output is valid), HP_EAGAIN while
  * pending, HP_ETIMEOUT if timeout_us elapsed (timeout_us < 0 waits without limit
  * on the host; the device side never spins), or an error. */
 hp_status hp_serve_poll(hp_server *s, uint64_t ticket, int timeout_us);
 
-/* Latency percentiles (microseconds, arrival to observed completion) and
+/* Latency percentiles (microseconds, arrival to observed completion; arrival
+ * is the scheduled time given to hp_serve_submit_at, else the submit call) and
  * throughput (requests/s) over all completed requests. */
 hp_status hp_serve_stats(const hp_server *s, double *p50_us, double *p99_us, double *p999_us,
                          double *nests_per_s);

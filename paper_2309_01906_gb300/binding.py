@@ -40,6 +40,7 @@ BODIES = {"load": HP_BODY_LOAD, "dot_bcast": HP_BODY_DOT_BCAST, "csr_gather": HP
 EXPORTED = ["hp_nest_create", "hp_nest_run", "hp_nest_run_host", "hp_nest_run_static", "hp_nest_run_batch",
             "hp_nest_tune", "hp_nest_tune_req", "hp_nest_error_bound",
             "hp_nest_describe", "hp_nest_check", "hp_nest_destroy", "hp_serve_create", "hp_serve_submit",
+            "hp_serve_submit_at", "hp_serve_clock_us",
             "hp_serve_poll", "hp_serve_stats", "hp_serve_counters", "hp_serve_destroy", "hp_set_option", "hp_get_option",
             "hp_last_error", "hp_version", "hp_stencil_create", "hp_stencil_run", "hp_stencil_describe",
             "hp_stencil_check", "hp_stencil_destroy", "hp_level_properties", "hp_level_select",
@@ -124,6 +125,10 @@ def lib() -> ctypes.CDLL:
         L.hp_serve_create.argtypes = [ctypes.c_size_t, i32, i32, ctypes.POINTER(p)]
         L.hp_serve_submit.restype = i32
         L.hp_serve_submit.argtypes = [p, p, p, p, ctypes.POINTER(u64)]
+        L.hp_serve_submit_at.restype = i32
+        L.hp_serve_submit_at.argtypes = [p, p, p, p, ctypes.c_double, ctypes.POINTER(u64)]
+        L.hp_serve_clock_us.restype = ctypes.c_double
+        L.hp_serve_clock_us.argtypes = []
         L.hp_serve_poll.restype = i32
         L.hp_serve_poll.argtypes = [p, u64, i32]
         L.hp_serve_stats.restype = i32
@@ -318,6 +323,17 @@ def hp_serve_submit(server, nest, in_ptrs, out_ptr) -> int:
     _check(lib().hp_serve_submit(server, nest, _ptr_array(in_ptrs), out_ptr or None, ctypes.byref(t)),
            "hp_serve_submit")
     return t.value
+
+
+def hp_serve_submit_at(server, nest, in_ptrs, out_ptr, arrival_us) -> int:
+    t = ctypes.c_uint64()
+    _check(lib().hp_serve_submit_at(server, nest, _ptr_array(in_ptrs), out_ptr or None, float(arrival_us),
+                                    ctypes.byref(t)), "hp_serve_submit_at")
+    return t.value
+
+
+def hp_serve_clock_us() -> float:
+    return float(lib().hp_serve_clock_us())
 
 
 def hp_serve_poll(server, ticket, timeout_us=0) -> int:

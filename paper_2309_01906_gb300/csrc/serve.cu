@@ -99,7 +99,7 @@ struct Request {
   hp_nest* nest;
   const void* in[2];
   void* out;
-  double t_submit;
+ double t_submit;        // arrival: scheduled (hp_serve_submit_at) or the submit call
   size_t bytes;          // inputs + outputs + scratch counted against the budget
   size_t part_bytes, ticket_bytes;
   size_t part_off, ticket_off;
@@ -406,8 +406,11 @@ hp_status hp_serve_create(size_t mem_budget_bytes, int max_slots, int n_streams,
   return HP_OK;
 }
 
-hp_status hp_serve_submit(hp_server* s, const hp_nest* shape, const void* const* in_dev, void* out_dev,
-                          uint64_t* ticket) {
+namespace {
+
+// arrival_us < 0: the request arrives now (latency counted from the call)
+hp_status submit(hp_server* s, const hp_nest* shape, const void* const* in_dev, void* out_dev, double arrival_us,
+                 uint64_t* ticket) {
   if (!s || !shape || !ticket) return fail(HP_EINVAL, "NULL argument");
   hp_nest* n = const_cast<hp_nest*>(shape);
   if (n->kind != NEST_RECT) return fail(HP_EUNSUPPORTED, "served nests must be rectangular");
@@ -432,7 +435,9 @@ hp_status hp_serve_submit(hp_server* s, const hp_nest* shape, const void* const*
   r.state = RQ_QUEUED;
   std::lock_guard<std::mutex> lock(s->mu);
   if (!s->error.empty()) return fail(HP_ECUDA, s->error);
-  r.t_submit = now_us();
+  const double t = now_us();
+  if (arrival_us > t) return fail(HP_EINVAL, "hp_serve_submit_at: the arrival time lies in the future");
+  r.t_submit = arrival_us >= 0.0 ? arrival_us : t;
   if (s->reqs.empty()) s->t_first = r.t_submit;
   r.ticket = s->reqs.size() + 1;
   s->reqs.push_back(r);
@@ -440,6 +445,21 @@ hp_status hp_serve_submit(hp_server* s, const hp_nest* shape, const void* const*
   s->queue.push_back(*ticket);
   return HP_OK;
 }
+
+}  // namespace
+
+hp_status hp_serve_submit(hp_server* s, const hp_nest* shape, const void* const* in_dev, void* out_dev,
+                          uint64_t* ticket) {
+  return submit(s, shape, in_dev, out_dev, -1.0, ticket);
+}
+
+hp_status hp_serve_submit_at(hp_server* s, const hp_nest* shape, const void* const* in_dev, void* out_dev,
+                             double arrival_us, uint64_t* ticket) {
+  if (!(arrival_us >= 0.0)) return fail(HP_EINVAL, "hp_serve_submit_at: arrival time must be >= 0");
+  return submit(s, shape, in_dev, out_dev, arrival_us, ticket);
+}
+
+double hp_serve_clock_us(void) { return now_us(); }
 
 hp_status hp_serve_poll(hp_server* s, uint64_t ticket, int timeout_us) {
   if (!s) return fail(HP_EINVAL, "server is NULL");

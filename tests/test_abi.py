@@ -198,3 +198,14 @@ def test_binding_enums_match_the_header():
         assert e["HP_PROP_" + k.upper()] == v, k
     for i, name in enumerate(hb.STATUS_NAMES):
         assert e[name] == i
+
+
+def test_serve_clock_is_monotonic_and_host_only():
+    # the serving clock needs no GPU; latency from scheduled arrival is measured on it
+    import time
+    a = hb.hp_serve_clock_us()
+    time.sleep(0.002)
+    b = hb.hp_serve_clock_us()
+    assert b - a >= 1500.0
+    # steady clock in microseconds: same epoch as the host's monotonic clock
+    assert abs(hb.hp_serve_clock_us() - time.monotonic() * 1e6) < 1e6

@@ -182,14 +182,20 @@ def test_gemv_workload_full_size():
 
 
 @pytest.mark.slow
-def test_four_level_workload_full_size():
-    # 64 x 512 x 16 x 1024 (2 GiB), all 32768 outputs against the oracle
+@pytest.mark.parametrize("which", ["bench_map", "cluster8_cta8"])
+def test_four_level_workload_full_size(which):
+    # 64 x 512 x 16 x 1024 (2 GiB), all 32768 outputs against the oracle, under
+    # the map bench.py times (cluster of 4 CTAs x 4 warps x 4 vector slots, the
+    # pipelined cluster kernel) and under a cluster of 8 x 8 warps
+    import bench
     A, w = synth.nest4_f32()
-    lm = [("grid", 0, 0), ("grid", 0, 0), ("cluster", 8, 0), ("cta", 8, 0)]
+    lm = bench.LEVEL_MAP if which == "bench_map" else [("grid", 0, 0), ("grid", 0, 0), ("cluster", 8, 0), ("cta", 8, 0)]
     ref = oracle.rect([64, 512, 16, 1024], 2, "sum", "f32", "dot_bcast", A=A, w=w)
     for prec in ("f32_comp", "f32"):
-        got, _, bound = gpu_rect([64, 512, 16, 1024], 2, "sum", prec, "dot_bcast", lm, A=A, w=w)
-        assert_close(got, ref, prec, "sum", bound, what=f"4-level full {prec}")
+        got, plan, bound = gpu_rect([64, 512, 16, 1024], 2, "sum", prec, "dot_bcast", lm, A=A, w=w)
+        if which == "bench_map":
+            assert (plan["cluster"], plan["warps"], plan["vec"], plan["grid_parts"], plan["pipe"]) == (4, 4, 4, 1, 1)
+        assert_close(got, ref, prec, "sum", bound, what=f"4-level full {prec} {which}")
 
 
 def test_kernel_attributes_shared_between_nests():

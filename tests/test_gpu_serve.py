@@ -133,3 +133,30 @@ def test_plain_mode_and_poll_semantics():
         hb.hp_serve_destroy(batched)
         for it in pool:
             it["nest"].close()
+
+
+def test_latency_counts_from_scheduled_arrival():
+    # a request whose arrival was scheduled 50 ms before its submission carries
+    # those 50 ms in its latency; an arrival in the future is refused
+    import torch
+    pool = _pool(4, seed=504)
+    server = hb.hp_serve_create(8 << 30, 64, 2)
+    try:
+        it = pool[0]
+        out = torch.empty(it["O"], dtype=it["dt"], device="cuda")
+        due = hb.hp_serve_clock_us() - 50_000.0
+        t = hb.hp_serve_submit_at(server, it["nest"].handle, [it["dA"].data_ptr()], out.data_ptr(), due)
+        assert hb.hp_serve_poll(server, t, -1) == hb.HP_OK
+        assert hb.hp_serve_stats(server)["p50_us"] >= 50_000.0
+        with pytest.raises(hb.HPError) as e:
+            hb.hp_serve_submit_at(server, it["nest"].handle, [it["dA"].data_ptr()], out.data_ptr(),
+                                  hb.hp_serve_clock_us() + 1e6)
+        assert e.value.status == hb.HP_EINVAL
+        single = torch.empty(it["O"], dtype=it["dt"], device="cuda")
+        it["nest"].run([it["dA"].data_ptr()], single.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert torch.equal(out, single)
+    finally:
+        hb.hp_serve_destroy(server)
+        for p in pool:
+            p["nest"].close()
