@@ -262,6 +262,21 @@ hp_status hp_nest_create(int depth, const int64_t *extents, const int64_t *csr_o
 hp_status hp_nest_run(hp_nest *n, const void *const *in_dev, void *out_dev, void *stream);
 
 /*
+ * hp_nest_run of a compensated FP32 sum (HP_F32_COMP, HP_RED_SUM, rectangular)
+ * that also writes, for each output, the FP32 compensation of its final
+ * rounding: comp_dev[o] is the exact error of out_dev[o] against the
+ * two-word sum s + c the reduction tree reached (Sec. 2's recursive
+ * reduction, carried in Ogita-Rump-Oishi double-word form), or, when the
+ * plan combines grid parts in FP64, the FP64 sum minus out_dev[o] rounded
+ * once.  out + comp then carries the result to about 2^-48 relative; |comp|
+ * is what the FP32 output gave away, for a caller's own error report.
+ *   comp_dev  device pointer, one float per output (same layout as out_dev).
+ * out_dev holds the same bits as hp_nest_run's.  HP_EUNSUPPORTED for other
+ * nests; otherwise as hp_nest_run.
+ */
+hp_status hp_nest_run_comp(hp_nest *n, const void *const *in_dev, void *out_dev, void *comp_dev, void *stream);
+
+/*
  * End-to-end run with HOST buffers: copies the inputs to device staging
  * buffers owned by the nest, runs, copies the outputs back, and waits for the
  * stream.  in_host / out_host are host pointers (pinned memory is fastest).

@@ -37,7 +37,7 @@ BODIES = {"load": HP_BODY_LOAD, "dot_bcast": HP_BODY_DOT_BCAST, "csr_gather": HP
           "affine": HP_BODY_AFFINE, "geometric": HP_BODY_GEOMETRIC}
 
 # every entry point include/hp.h declares
-EXPORTED = ["hp_nest_create", "hp_nest_run", "hp_nest_run_host", "hp_nest_run_static", "hp_nest_run_batch",
+EXPORTED = ["hp_nest_create", "hp_nest_run", "hp_nest_run_comp", "hp_nest_run_host", "hp_nest_run_static", "hp_nest_run_batch",
             "hp_nest_tune", "hp_nest_tune_req", "hp_nest_error_bound",
             "hp_nest_describe", "hp_nest_check", "hp_nest_destroy", "hp_serve_create", "hp_serve_submit",
             "hp_serve_submit_at", "hp_serve_clock_us",
@@ -105,6 +105,8 @@ def lib() -> ctypes.CDLL:
         L.hp_nest_create.argtypes = [i32, p, p, i64, p, i32, i32, i32, i32, p, ctypes.POINTER(p)]
         L.hp_nest_run.restype = i32
         L.hp_nest_run.argtypes = [p, p, p, p]
+        L.hp_nest_run_comp.restype = i32
+        L.hp_nest_run_comp.argtypes = [p, p, p, p, p]
         L.hp_nest_run_host.restype = i32
         L.hp_nest_run_host.argtypes = [p, p, p, p]
         L.hp_nest_run_static.restype = i32
@@ -229,6 +231,12 @@ def hp_nest_create(depth, extents, csr_offsets, n_rows, level_map, op, red_level
 def hp_nest_run(nest, in_ptrs, out_ptr, stream=0):
     st = lib().hp_nest_run(nest, _ptr_array(in_ptrs), out_ptr or None, stream or None)
     _check(st, "hp_nest_run")
+
+
+def hp_nest_run_comp(nest, in_ptrs, out_ptr, comp_ptr, stream=0):
+    """hp_nest_run of a compensated FP32 sum that also writes each output's residual."""
+    st = lib().hp_nest_run_comp(nest, _ptr_array(in_ptrs), out_ptr or None, comp_ptr or None, stream or None)
+    _check(st, "hp_nest_run_comp")
 
 
 def hp_nest_run_host(nest, in_host_ptrs, out_host_ptr, stream=0):
@@ -483,6 +491,9 @@ class Nest:
 
     def run(self, in_ptrs, out_ptr, stream=0):
         hp_nest_run(self.handle, in_ptrs, out_ptr, stream)
+
+    def run_comp(self, in_ptrs, out_ptr, comp_ptr, stream=0):
+        hp_nest_run_comp(self.handle, in_ptrs, out_ptr, comp_ptr, stream)
 
     def run_static(self, in_ptrs, out_ptr, stream=0):
         hp_nest_run_static(self.handle, in_ptrs, out_ptr, stream)

@@ -74,6 +74,12 @@ struct OpF32Comp {
     return {__shfl_xor_sync(0xffffffffu, a.s, m, w), __shfl_xor_sync(0xffffffffu, a.c, m, w)};
   }
   __device__ static Out finish(Acc a) { return __fadd_rn(a.s, a.c); }
+  // exact error of finish(): finish(a) + residual(a) == a.s + a.c (TwoSum)
+  __device__ static float residual(Acc a) {
+    float s, e;
+    two_sum(a.s, a.c, s, e);
+    return e;
+  }
 };
 
 struct OpF32Max {

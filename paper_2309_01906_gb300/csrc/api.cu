@@ -75,7 +75,9 @@ hp_status run_rect(hp_nest* n, const void* const* in_dev, void* out_dev, cudaStr
 }
 
 // run with caller-provided grid-part scratch (a server's per-request scratch)
-hp_status run_rect_with(hp_nest* n, const void* const* in_dev, void* out_dev, void* part, cudaStream_t st) {
+// and, for compensated sums, an optional residual output
+hp_status run_rect_with(hp_nest* n, const void* const* in_dev, void* out_dev, void* part, cudaStream_t st,
+                        float* comp) {
   const NestPlan& p = n->plan;
   for (int i = 0; i < p.n_inputs; ++i) {
     if (!in_dev || !in_dev[i]) return fail(HP_EINVAL, "missing device input " + std::to_string(i));
@@ -84,7 +86,7 @@ hp_status run_rect_with(hp_nest* n, const void* const* in_dev, void* out_dev, vo
   }
   if (!out_dev && p.rp.O > 0) return fail(HP_EINVAL, "out_dev is NULL");
   if (p.rp.G > 1 && p.rp.items > 0 && !part) return fail(HP_EINVAL, "grid-split plan without partial scratch");
-  RectArgs a{in_dev, out_dev, part, n->geo, st};
+  RectArgs a{in_dev, out_dev, part, n->geo, st, comp};
   const bool fp = p.prec == HP_F32 || p.prec == HP_F32_COMP;
   switch (p.op) {
     case HP_RED_SUM:
@@ -220,6 +222,18 @@ hp_status hp_nest_run(hp_nest* n, const void* const* in_dev, void* out_dev, void
   if (n->kind == NEST_ORDERED) return run_ordered(n, in_dev, out_dev, s);
   if (n->kind == NEST_NARROW) return run_narrow(n, in_dev, out_dev, s);
   return run_csr(n, in_dev, out_dev, s);
+}
+
+hp_status hp_nest_run_comp(hp_nest* n, const void* const* in_dev, void* out_dev, void* comp_dev, void* stream) {
+  if (!n) return fail(HP_EINVAL, "nest is NULL");
+  if (n->kind != NEST_RECT || n->plan.prec != HP_F32_COMP || n->plan.op != HP_RED_SUM)
+    return fail(HP_EUNSUPPORTED, "hp_nest_run_comp takes rectangular compensated FP32 sums (HP_F32_COMP, HP_RED_SUM)");
+  const RectPlan& rp = n->plan.rp;
+  if (!comp_dev && rp.O > 0) return fail(HP_EINVAL, "comp_dev is NULL");
+  hp_status st = ensure_device(n);
+  if (st != HP_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return run_rect_with(n, in_dev, out_dev, n->part, s, static_cast<float*>(comp_dev));
 }
 
 hp_status hp_nest_run_host(hp_nest* n, const void* const* in_host, void* out_host, void* stream) {

@@ -39,7 +39,8 @@ uint64_t next_plan_id();
 void batch_forget(const hp_nest* n);   // drop cached batch contexts that contain n
 hp_status ensure_device(hp_nest* n);
 hp_status run_rect(hp_nest* n, const void* const* in_dev, void* out_dev, cudaStream_t st);
-hp_status run_rect_with(hp_nest* n, const void* const* in_dev, void* out_dev, void* part, cudaStream_t st);
+hp_status run_rect_with(hp_nest* n, const void* const* in_dev, void* out_dev, void* part, cudaStream_t st,
+                        float* comp = nullptr);
 size_t out_bytes(const hp_nest* n);
 double error_bound(const hp_nest* n);
 

@@ -54,6 +54,7 @@ struct RectPlan {
   int32_t groups;          // element groups per thread per item (max over threads)
   int32_t geo_m;
   int64_t aff_a, aff_b, aff_m;
+  float* comp;             // compensated FP32 sums: optional residual output (out + comp = s + c), or null
 };
 
 // Host-side description of one rectangular nest's plan.

@@ -235,8 +235,14 @@ __device__ __forceinline__ typename Op::Acc lanes_allreduce(typename Op::Acc a, 
 template <class Op>
 __device__ __forceinline__ void emit(const RectPlan& p, int64_t item, typename Op::Acc a, typename Op::Out* out,
                                      typename Op::Acc* part) {
-  if (p.G == 1) out[item] = Op::finish(a);
-  else part[item] = a;
+  if (p.G == 1) {
+    out[item] = Op::finish(a);
+    if constexpr (std::is_same_v<typename Op::Acc, f2>) {
+      if (p.comp) p.comp[item] = Op::residual(a);
+    }
+  } else {
+    part[item] = a;
+  }
 }
 
 // ---------------------------------------------------------------- team = cluster or CTA
@@ -537,7 +543,8 @@ __global__ void __launch_bounds__(1024) rect_lanes_kernel(RectPlan p, Body body,
 
 // ---------------------------------------------------------------- grid parts -> outputs
 template <class Op>
-__global__ void rect_combine_kernel(int64_t O, int32_t G, const typename Op::Acc* part, typename Op::Out* out) {
+__global__ void rect_combine_kernel(int64_t O, int32_t G, const typename Op::Acc* part, typename Op::Out* out,
+                                    float* comp) {
   for (int64_t o = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; o < O;
        o += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const typename Op::Acc* pp = part + o * G;
@@ -549,7 +556,10 @@ __global__ void rect_combine_kernel(int64_t O, int32_t G, const typename Op::Acc
         s += static_cast<double>(v.s);
         s += static_cast<double>(v.c);
       }
-      out[o] = static_cast<float>(s);
+      const float r = static_cast<float>(s);
+      out[o] = r;
+      // the FP64 remainder, rounded once (out + comp carries the FP64 sum to ~2^-48)
+      if (comp) comp[o] = static_cast<float>(s - static_cast<double>(r));
     } else {
       typename Op::Acc a = pp[0];
       for (int g = 1; g < G; ++g) a = Op::combine(a, pp[g]);
@@ -566,6 +576,9 @@ __global__ void rect_map_kernel(RectPlan p, Body body, typename Op::Out* out) {
     typename Op::Acc acc[1] = {Op::ident()};
     body.template fold<1>(acc, f, 0);
     out[f] = Op::finish(acc[0]);
+    if constexpr (std::is_same_v<typename Op::Acc, f2>) {
+      if (p.comp) p.comp[f] = Op::residual(acc[0]);
+    }
   }
 }
 

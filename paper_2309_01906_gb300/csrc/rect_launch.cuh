@@ -19,6 +19,7 @@ struct RectArgs {
   void* part;              // grid-part partials (G > 1)
   const float* geo;        // GEOMETRIC table (device)
   cudaStream_t stream;
+  float* comp = nullptr;   // compensated sums: residual output (hp_nest_run_comp), or null
 };
 
 inline hp_status cuda_fail(cudaError_t e, const char* what) {
@@ -30,6 +31,7 @@ hp_status launch_team(const NestPlan& np, RectPlan rp, LaunchCfg& cfg, const Bod
   using Out = typename Op::Out;
   using Acc = typename Op::Acc;
   cudaError_t e;
+  rp.comp = a.comp;
   if (rp.team == TEAM_MAP) {
     auto k = rect_map_kernel<Op, Body>;
     if (!cfg.ready) {
@@ -151,7 +153,7 @@ hp_status launch_team(const NestPlan& np, RectPlan rp, LaunchCfg& cfg, const Bod
     if (e != cudaSuccess) return cuda_fail(e, "rect_lanes_kernel launch");
   }
   if (rp.G > 1) {
-    rect_combine_kernel<Op><<<cfg.combine_grid, 256, 0, a.stream>>>(rp.O, rp.G, part, out);
+    rect_combine_kernel<Op><<<cfg.combine_grid, 256, 0, a.stream>>>(rp.O, rp.G, part, out, a.comp);
     e = cudaPeekAtLastError();
     if (e != cudaSuccess) return cuda_fail(e, "rect_combine_kernel launch");
   }

@@ -37,7 +37,6 @@
 
 namespace hp {
 
-hp_status run_rect_with(hp_nest* n, const void* const* in_dev, void* out_dev, void* part, cudaStream_t st);
 const std::string& last_error_string();
 
 namespace {

@@ -208,3 +208,50 @@ def test_kernel_attributes_shared_between_nests():
     gpu_rect([3, 7, 16, 1024], 2, "sum", "f32_comp", "dot_bcast", lm_b, A=A, w=w)
     again = gpu_rect([3, 7, 16, 1024], 2, "sum", "f32_comp", "dot_bcast", lm_a, A=A, w=w)[0]
     assert np.array_equal(first, again)
+
+
+@pytest.mark.parametrize("ext,r,lm", [
+    ([37, 1029], 1, None),
+    ([37, 1028], 1, ["grid", "warp"]),
+    ([3, 7, 16, 132], 2, [("grid", 0, 0), ("grid", 0, 0), ("cluster", 8, 0), ("cta", 8, 0)]),   # pipelined cluster
+    ([7, 1 << 16], 1, [("grid", 0, 0), ("grid", 0, 4096)]),                                    # FP64 grid combine
+    ([5, 300], 1, ["grid", ("subwarp", 8, 0)]),
+    ([6, 5], 2, None),                                                                          # no reduction
+])
+def test_compensation_output(ext, r, lm):
+    # hp_nest_run_comp: the outputs are hp_nest_run's bits; comp is the exact
+    # residual of each output's final rounding, so |comp| <= ulp/2 and out + comp
+    # is far closer to the FP64 oracle than out alone
+    import torch
+    from paper_2309_01906_gb300 import binding as hb
+    A, w = _inputs(ext, r, "f32_comp", "dot_bcast")
+    O = int(np.prod(ext[:r]))
+    n = hb.Nest(ext, r, "sum", "f32_comp", "dot_bcast", level_map=lm)
+    try:
+        dA, dw = torch.from_numpy(A).cuda(), torch.from_numpy(w).cuda()
+        out = torch.empty(O, dtype=torch.float32, device="cuda")
+        out2 = torch.empty_like(out)
+        comp = torch.full((O,), float("nan"), dtype=torch.float32, device="cuda")
+        s = torch.cuda.current_stream().cuda_stream
+        n.run([dA.data_ptr(), dw.data_ptr()], out.data_ptr(), s)
+        n.run_comp([dA.data_ptr(), dw.data_ptr()], out2.data_ptr(), comp.data_ptr(), s)
+        torch.cuda.synchronize()
+        bound = n.error_bound()
+    finally:
+        n.close()
+    o, o2, c = out.cpu().numpy(), out2.cpu().numpy(), comp.cpu().numpy()
+    assert np.array_equal(o, o2)
+    assert np.all(np.isfinite(c))
+    ulp = np.spacing(np.abs(o).astype(np.float32)).astype(np.float64)
+    assert np.all(np.abs(c.astype(np.float64)) <= 0.5 * ulp)
+    ref = oracle_rect(ext, r, "sum", "f32_comp", "dot_bcast", A=A, w=w)
+    dw_err = np.abs(o.astype(np.float64) + c.astype(np.float64) - ref.values)
+    out_err = np.abs(o.astype(np.float64) - ref.values)
+    # the two-word result carries the reduction tree's error only (no final FP32 rounding)
+    lim = max(bound - 2.0 ** -24, 0.0) * ref.abs_sum + 2.0 ** -46 * np.abs(ref.values) + 1e-300
+    assert np.all(dw_err <= lim), (dw_err.max(), lim.min())
+    if r < len(ext):
+        assert np.median(dw_err) <= 1e-3 * max(np.median(out_err), 1e-300) or np.median(out_err) == 0
+    else:
+        # one body value per output: out + comp is the exact FP32 x FP32 product
+        assert np.all(dw_err == 0)
