@@ -11,8 +11,8 @@ One step = one run of the nest (all its launches) over the resident inputs.
 Metric: nest iterations per second (2^29 iterations per step).  The line also
 carries the per-result error of every output the CPU-baseline leg evaluated
 against the FP64 oracle (`parity`), and, after the headline's timed region,
-the GEMV-shaped nest, the 10,000-nest batch and 10 s of Poisson serving
-(`workloads`; --extras none leaves them out).
+the GEMV-shaped nest, the ragged CSR nest, the 10,000-nest batch and 10 s of
+Poisson serving (`workloads`; --extras none leaves them out).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hp|reference]
 
@@ -54,10 +54,12 @@ R = EXTENTS[2] * EXTENTS[3]
 # algorithmic bytes of one launch: A once, w once, outputs once
 ALG_BYTES = ITERS * 4 + R * 4 + N_OUT * 4
 WORKLOAD = "4-level nest b=64 i=512 j=16 k=1024, out[b][i]=sum_j sum_k A[b][i][j][k]*w[j][k]"
-# DRAM traffic of one launch from an ncu capture (profiles/rect_block_pipe_4level_nest.md),
-# valid only while the kernel sources still hash to the fingerprint it was taken at
+# DRAM traffic of one launch (dram__bytes_read.sum + dram__bytes_write.sum) taken from
+# an ncu capture of this workload, not measured by this script; reported only while
+# the kernel sources still hash to the fingerprint the capture was taken at
 TRAFFIC = {"sources": ["paper_2309_01906_gb300/csrc/rect_kernels.cuh", "paper_2309_01906_gb300/csrc/accum.cuh"],
-           "sha256_16": "75e0c8599af476fd", "bytes_per_launch": 2194.9e6}
+           "sha256_16": "75e0c8599af476fd", "bytes_per_launch": 2194.9e6,
+           "how": "taken from an ncu capture of one launch (null once the kernel sources changed since)"}
 
 
 def traffic_per_launch():
@@ -358,6 +360,7 @@ def run_hp(args):
                 "unit": "GB/s",
                 "frac": achieved / peak,
                 "traffic": traffic_per_launch(),
+                "traffic_source": TRAFFIC["how"],
                 "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": ALG_BYTES,
                 "kernel": plan["kernel"],
@@ -516,17 +519,26 @@ def _event_time(fn, steps, warmup, stream, flush=None):
     return float(np.mean([a.elapsed_time(b) for a, b in per]))
 
 
-def run_csr_workload(args):
+def csr_measure(args):
     """Ragged CSR nest: 2^22 rows (or --csr-rows), Zipf(1.5) lengths clipped to
     [1, 65536], col uniform in [0, 2^22), FP32 normal val / x, compensated SpMV
-    with the int64 histogram of col >> 10 fused into the same sweep."""
+    with the int64 histogram of col >> 10 fused into the same sweep.
+
+    Two rooflines: HBM (the algorithmic bytes) and the x gathers, whose random
+    4-byte reads each take one 32-byte L2 sector: their rate is measured on
+    this GPU by a gather-only kernel (hp_probe_gather, the same loads, as many
+    reads as the nest has entries, on the same x).  The CPU-baseline leg runs
+    the oracle on 1024 seeded rows and the whole histogram; parity compares the
+    rows within tolerance and the histogram bit for bit."""
     import torch
 
     from paper_2309_01906_gb300 import binding as hb
     from paper_2309_01906_gb300 import synth
     n_rows = args.csr_rows
     n_cols = 1 << 22
+    t0 = time.perf_counter()
     csr = synth.csr_zipf(n_rows=n_rows, n_cols=n_cols)
+    setup_s = time.perf_counter() - t0
     n_bins = n_cols >> 10
     d = [torch.from_numpy(a).cuda() for a in (csr.offsets, csr.col, csr.val, csr.x)]
     y = torch.empty(n_rows, dtype=torch.float32, device="cuda")
@@ -535,24 +547,59 @@ def run_csr_workload(args):
     n = hb.Nest(csr_rows=n_rows, red_level=1, op="sum", prec=args.prec, body="csr_gather", params=p)
     stream = torch.cuda.Stream()
     ins = [t.data_ptr() for t in d] + [h.data_ptr()]
-    ms = _event_time(lambda: n.run(ins, y.data_ptr(), stream.cuda_stream), args.steps, args.warmup, stream)
+    steps = max(3, min(args.steps, 20))
+    ms = _event_time(lambda: n.run(ins, y.data_ptr(), stream.cuda_stream), steps, args.warmup, stream)
     assert n.check(stream.cuda_stream) == 0
+    # gather-only probe: as many random reads of the same x as the nest has entries
+    psum = torch.zeros(1, dtype=torch.float32, device="cuda")
+    ms_probe = _event_time(lambda: hb.hp_probe_gather(d[3].data_ptr(), n_cols, csr.nnz, 7, psum.data_ptr(),
+                                                      stream.cuda_stream), steps, args.warmup, stream)
     alg = 8 * csr.nnz + 8 * (n_rows + 1) + 4 * n_cols + 4 * n_rows + 8 * n_bins
     peak, kind = measured_peaks()
     lens = np.diff(csr.offsets)
-    print(json.dumps({
+    gather_rate = csr.nnz / (ms_probe * 1e-3)
+    parity, cpu = None, None
+    if not args.no_cpu_baseline:
+        import oracle
+        g = np.random.Generator(np.random.PCG64(23))
+        rows = np.sort(g.choice(n_rows, size=min(n_rows, 1024), replace=False))
+        # the longest rows too: they take the split (grid-part) path
+        rows = np.unique(np.concatenate([rows, np.argsort(lens)[-16:]]))
+        t1 = time.perf_counter()
+        ref = oracle.csr(csr.offsets, csr.col, csr.val, csr.x, rows=rows)
+        dt = time.perf_counter() - t1
+        got = y.cpu().numpy()[rows]
+        parity = {"rows": fp_parity(got, ref, args.prec, n.error_bound(), 1e-6 if args.prec == "f32_comp" else 1e-5)}
+        cpu = {"value": float(lens[rows].sum()) / dt, "unit": "entries/s", "cores": 1, "kind": "oracle",
+               "sample": f"{rows.size} rows ({int(lens[rows].sum())} entries): 1024 seeded + the 16 longest"}
+        if not args.no_hist:
+            hr = oracle.hist(csr.col, 10, n_bins)
+            parity["histogram_bit_exact"] = bool(np.array_equal(h.cpu().numpy(), hr.values) and hr.overflow == 0)
+            parity["histogram_total"] = int(hr.values.sum())
+    res = {
         "workload": f"CSR {n_rows} rows, Zipf(1.5) clipped [1,65536], nnz {csr.nnz}, SpMV"
                     + ("" if args.no_hist else " + fused int64 histogram"),
         "metric": "nest iterations/s", "value": csr.nnz / (ms * 1e-3), "unit": "iterations/s",
-        "ms_per_step": ms, "prec": args.prec, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "prec": args.prec, "steps": steps, "warmup": args.warmup,
         "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": alg / (ms * 1e-3) / 1e9 / peak, "peak_kind": kind, "algorithmic_bytes": alg},
-        "x_gather_sector_bytes": 32 * csr.nnz,
+        "roofline_gather": {"bound": "l2_sectors", "achieved": csr.nnz / (ms * 1e-3), "peak": gather_rate,
+                            "unit": "gathers/s (one 32-byte L2 sector each)", "frac": (csr.nnz / (ms * 1e-3)) / gather_rate,
+                            "peak_kind": "measured by hp_probe_gather on this GPU (same x, nnz random reads)",
+                            "probe_ms": ms_probe, "sector_bytes": 32 * csr.nnz,
+                            "sector_gbs": 32 * csr.nnz / (ms * 1e-3) / 1e9,
+                            "probe_sector_gbs": 32 * gather_rate / 1e9},
         "rows_by_class": [int(np.sum(lens <= 4)), int(np.sum((lens > 4) & (lens <= 32))),
                           int(np.sum((lens > 32) & (lens <= 1024))), int(np.sum((lens > 1024) & (lens <= 16384))),
                           int(np.sum(lens > 16384))],
-        "l2": "inputs larger than L2; no flush"}))
+        "parity": parity, "cpu_baseline": cpu, "setup_s": setup_s,
+        "l2": "inputs larger than L2; no flush (x, 16 MiB, stays in L2 by design)"}
     n.close()
+    return res
+
+
+def run_csr_workload(args):
+    print(json.dumps(csr_measure(args)))
 
 
 def gemv_measure(args):
@@ -1113,7 +1160,7 @@ def run_serve_workload(args):
     print(json.dumps(serve_measure(args)))
 
 
-EXTRAS = {"gemv": lambda a: gemv_measure(a), "batch": lambda a: batch_measure(a),
+EXTRAS = {"gemv": lambda a: gemv_measure(a), "csr": lambda a: csr_measure(a), "batch": lambda a: batch_measure(a),
           "serve": lambda a: serve_measure(a)}
 
 
@@ -1149,9 +1196,9 @@ def main():
                     help="serve: seconds of arrivals (60 for --workload serve, 10 inside the headline line)")
     ap.add_argument("--serve-pool", type=int, default=2000)
     ap.add_argument("--no-hist", action="store_true", help="csr: SpMV without the fused histogram")
-    ap.add_argument("--extras", default="gemv,batch,serve",
+    ap.add_argument("--extras", default="gemv,csr,batch,serve",
                     help="nest4: other workloads measured after the headline and added to its line "
-                         "(comma list of gemv, batch, serve; 'none' for the headline alone)")
+                         "(comma list of gemv, csr, batch, serve; 'none' for the headline alone)")
     ap.add_argument("--parity-out", default="", help="nest4: write the per-result error table (CSV) here")
     ap.add_argument("--batch-check", type=int, default=256, help="batch: nests compared with the oracle")
     ap.add_argument("--batch-plain-steps", type=int, default=3, help="batch: timed passes of one launch per nest")

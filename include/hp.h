@@ -356,6 +356,20 @@ hp_status hp_nest_check(hp_nest *n, void *stream, int32_t *device_error);
 
 void hp_nest_destroy(hp_nest *n);
 
+/*
+ * Measurement aid for the roofline of ragged nests (not a step of the method):
+ * one kernel that reads n_gathers random 4-byte elements of x_dev[0 .. n_x)
+ * (indices uniform from a counter hash of (index, seed)) through the same
+ * loads as the CSR executor's x gathers (cached in L2 only), 8 independent
+ * reads in flight per thread, and writes their FP32 sum to *sum_dev (one
+ * float, device memory; zeroed first).  Timing it gives the rate at which
+ * this GPU serves random 32-byte L2 sectors to one 4-byte use each: the bound
+ * of the CSR body's x[col[e]] reads once x fits L2.  Asynchronous on stream;
+ * allocates nothing.  HP_EINVAL for n_x outside [1, 2^32) or NULL pointers.
+ */
+hp_status hp_probe_gather(const float *x_dev, int64_t n_x, int64_t n_gathers, uint32_t seed, float *sum_dev,
+                          void *stream);
+
 /* ---------------------------------------------------------------------- */
 /* Serving: continuous batching of nest requests under a device-memory budget.
  *

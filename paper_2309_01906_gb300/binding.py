@@ -40,7 +40,7 @@ BODIES = {"load": HP_BODY_LOAD, "dot_bcast": HP_BODY_DOT_BCAST, "csr_gather": HP
 EXPORTED = ["hp_nest_create", "hp_nest_run", "hp_nest_run_comp", "hp_nest_run_host", "hp_nest_run_static", "hp_nest_run_batch",
             "hp_nest_tune", "hp_nest_tune_req", "hp_nest_error_bound",
             "hp_nest_describe", "hp_nest_check", "hp_nest_destroy", "hp_serve_create", "hp_serve_submit",
-            "hp_serve_submit_at", "hp_serve_clock_us",
+            "hp_serve_submit_at", "hp_serve_clock_us", "hp_probe_gather",
             "hp_serve_poll", "hp_serve_stats", "hp_serve_counters", "hp_serve_destroy", "hp_set_option", "hp_get_option",
             "hp_last_error", "hp_version", "hp_stencil_create", "hp_stencil_run", "hp_stencil_describe",
             "hp_stencil_check", "hp_stencil_destroy", "hp_level_properties", "hp_level_select",
@@ -123,6 +123,8 @@ def lib() -> ctypes.CDLL:
         L.hp_nest_check.argtypes = [p, p, ctypes.POINTER(ctypes.c_int32)]
         L.hp_nest_destroy.restype = None
         L.hp_nest_destroy.argtypes = [p]
+        L.hp_probe_gather.restype = i32
+        L.hp_probe_gather.argtypes = [p, i64, i64, ctypes.c_uint32, p, p]
         L.hp_serve_create.restype = i32
         L.hp_serve_create.argtypes = [ctypes.c_size_t, i32, i32, ctypes.POINTER(p)]
         L.hp_serve_submit.restype = i32
@@ -318,6 +320,12 @@ def hp_nest_check(nest, stream=0) -> int:
 def hp_nest_destroy(nest):
     if nest:
         lib().hp_nest_destroy(nest)
+
+
+def hp_probe_gather(x_ptr, n_x, n_gathers, seed, sum_ptr, stream=0):
+    """Gather-rate probe: n_gathers random 4-byte reads of x (see include/hp.h)."""
+    _check(lib().hp_probe_gather(x_ptr, int(n_x), int(n_gathers), int(seed) & 0xffffffff, sum_ptr, stream or None),
+           "hp_probe_gather")
 
 
 def hp_serve_create(mem_budget_bytes, max_slots, n_streams):

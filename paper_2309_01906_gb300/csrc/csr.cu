@@ -701,6 +701,55 @@ hp_status run_csr(hp_nest* n, const void* const* in_dev, void* out_dev, cudaStre
   }
 }
 
+// ---------------------------------------------------------------- gather-rate probe
+namespace {
+
+// counter hash (murmur3's 32-bit finalizer over index ^ seed): uniform indices
+__device__ __forceinline__ uint32_t probe_hash(uint64_t i, uint32_t seed) {
+  uint32_t h = static_cast<uint32_t>(i) ^ static_cast<uint32_t>(i >> 32) * 0x9e3779b9u ^ seed;
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+
+// n random 4-byte reads of x through the CSR executor's x-gather path (__ldcg:
+// cached in L2 only), 8 independent reads in flight per thread per round;
+// each block adds its sum to *out so that no read is dead code
+__global__ void __launch_bounds__(256) gather_probe_kernel(const float* __restrict__ x, uint32_t n_x, int64_t n,
+                                                           uint32_t seed, float* out) {
+  __shared__ float wsum[8];
+  float acc = 0.0f;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  for (; i + 7 * stride < n; i += 8 * stride) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const uint32_t h = probe_hash(static_cast<uint64_t>(i + u * stride), seed);
+      v[u] = __ldcg(x + static_cast<uint32_t>((static_cast<uint64_t>(h) * n_x) >> 32));
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc += v[u];
+  }
+  for (; i < n; i += stride) {
+    const uint32_t h = probe_hash(static_cast<uint64_t>(i), seed);
+    acc += __ldcg(x + static_cast<uint32_t>((static_cast<uint64_t>(h) * n_x) >> 32));
+  }
+  for (int m = 16; m >= 1; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += wsum[w];
+    atomicAdd(out, t);
+  }
+}
+
+}  // namespace
+
 size_t csr_out_bytes(const hp_nest* n) {
   return n->csr.op == HP_RED_HIST_COUNT ? static_cast<size_t>(n->csr.n_bins) * 8
                                         : static_cast<size_t>(n->csr.n_rows) * 4;
@@ -722,3 +771,25 @@ void csr_release(hp_nest* n) {
 }
 
 }  // namespace hp
+
+extern "C" hp_status hp_probe_gather(const float* x_dev, int64_t n_x, int64_t n_gathers, uint32_t seed, float* sum_dev,
+                                     void* stream) {
+  using namespace hp;
+  if (!x_dev || !sum_dev) return fail(HP_EINVAL, "x_dev and sum_dev must be device pointers");
+  if (n_x < 1 || n_x > (int64_t(1) << 32) - 1) return fail(HP_EINVAL, "n_x must be in [1, 2^32)");
+  if (n_gathers < 0) return fail(HP_EINVAL, "n_gathers must be >= 0");
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gather_probe_kernel, 256, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "gather probe set-up");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  e = cudaMemsetAsync(sum_dev, 0, sizeof(float), st);
+  if (e != cudaSuccess) return cuda_fail(e, "gather probe memset");
+  if (n_gathers == 0) return HP_OK;
+  const int64_t want = (n_gathers + 255) / 256;
+  const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(want, static_cast<int64_t>(std::max(1, per_sm)) * sms)));
+  gather_probe_kernel<<<grid, 256, 0, st>>>(x_dev, static_cast<uint32_t>(n_x), n_gathers, seed, sum_dev);
+  e = cudaPeekAtLastError();
+  return e == cudaSuccess ? HP_OK : cuda_fail(e, "gather probe launch");
+}

@@ -5,9 +5,11 @@
 // order of the iterations they folded.  The lowering gives every warp a
 // contiguous range of iterations and folds it in rounds: in each round lane l
 // folds the l-th of 32 consecutive pieces sequentially (so the warp's loads
-// are coalesced), an xor butterfly whose masks grow 1, 2, ..., 16 joins the 32
-// pieces, at each level two adjacent ranks with the lower one first (Sec.
-// 3.7's sibling exchange), and the round joins the warp's running state.
+// are coalesced), a __shfl_down_sync tree at distances 1, 2, ..., 16 joins the
+// 32 pieces in order into lane 0 (at each level a lane's own range first, the
+// range of the lane at the given distance after it: Sec. 3.7's sibling
+// exchange, one combine per level), and the round joins the warp's running
+// state.
 // Warps of a CTA are combined by rank the same way, and the parts of an output
 // are folded in part order by the CTA that takes the last ticket.
 //

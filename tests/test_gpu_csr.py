@@ -129,3 +129,31 @@ def test_full_size_zipf(n_rows):
     assert_close(y[rows], ref, "f32_comp", "sum", what=f"full-size zipf {n_rows} sampled rows")
     href = oracle.hist(csr.col, 10, (1 << 22) >> 10)
     assert np.array_equal(h, href.values) and int(h.sum()) == csr.nnz
+
+
+def test_gather_probe_reads_what_its_hash_names():
+    # the gather-rate probe reads x at murmur3-finalizer indices of (i, seed),
+    # scaled to [0, n_x); with small integer values every FP32 sum is exact, so
+    # the device sum must equal the host sum of the same reads
+    import torch
+    from paper_2309_01906_gb300 import binding as hb
+
+    def idx(i, seed, n_x):
+        i = np.asarray(i, dtype=np.uint64)
+        h = (i & np.uint64(0xffffffff)) ^ (((i >> np.uint64(32)) * np.uint64(0x9e3779b9)) & np.uint64(0xffffffff))
+        h = (h ^ np.uint64(seed)) & np.uint64(0xffffffff)
+        for sh, mul in ((16, 0x85ebca6b), (13, 0xc2b2ae35)):
+            h ^= h >> np.uint64(sh)
+            h = (h * np.uint64(mul)) & np.uint64(0xffffffff)
+        h ^= h >> np.uint64(16)
+        return (h * np.uint64(n_x)) >> np.uint64(32)
+
+    for n_x, n in ((1 << 22, 123457), (1000, 5000), (7, 3)):
+        x = (np.arange(n_x) % 8).astype(np.float32)
+        dx = torch.from_numpy(x).cuda()
+        s = torch.full((1,), 123.0, dtype=torch.float32, device="cuda")
+        hb.hp_probe_gather(dx.data_ptr(), n_x, n, 42, s.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        ii = idx(np.arange(n), 42, n_x)
+        assert ii.max() < n_x
+        assert float(s.item()) == float(x[ii.astype(np.int64)].astype(np.float64).sum())
