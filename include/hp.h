@@ -305,10 +305,14 @@ hp_status hp_nest_run_host(hp_nest *n, const void *const *in_host, void *out_hos
 hp_status hp_nest_run_static(hp_nest *n, const void *const *in_dev, void *out_dev, void *stream);
 
 /*
- * Run many independent nests in one persistent launch (replayed from a cached
- * CUDA graph).  nests[i], in_dev[i], out_dev[i] as for hp_nest_run.  All nests
- * must be rectangular.  Each nest's outputs equal those of hp_nest_run on the
- * same nest bit for bit (same reduction tree).
+ * Run many independent nests in one persistent launch per arithmetic
+ * (replayed from a cached CUDA graph; the arithmetics' kernels are parallel
+ * branches of it).  nests[i], in_dev[i], out_dev[i] as for hp_nest_run.  All
+ * nests must be rectangular.  Each nest's outputs equal those of hp_nest_run
+ * on the same nest bit for bit (same reduction tree).  Nests whose plan is a
+ * cluster of CTAs (or a CTA of more than 8 warps), which the persistent
+ * kernel's single CTAs cannot run, are run with their own launches on the
+ * same stream after it.
  */
 hp_status hp_nest_run_batch(hp_nest *const *nests, const void *const *const *in_dev, void *const *out_dev,
                             int count, void *stream);
@@ -319,7 +323,11 @@ hp_status hp_nest_run_batch(hp_nest *const *nests, const void *const *const *in_
  * candidate levels and picks one at run time; here the pick is timed).
  * Candidates keep the output levels on the grid and bind every reduced level
  * to one hardware level (CTA of 4 or 8 warps, warp, sub-warp group of 2..16
- * lanes, the vector slots of a thread, a thread, or a split over grid parts);
+ * lanes, the vector slots of a thread, a thread, or a split over grid parts),
+ * or, for long reductions, the first reduced level to a cluster of 2, 4 or 8
+ * CTAs and the inner ones to a CTA (not in batched timing), or, with several
+ * reduced levels, the first to the warps of a CTA (or to grid parts) and the
+ * inner ones to the lanes of each warp (or to a CTA);
  * each is run on in_dev / out_dev on `stream` and timed with CUDA events.
  * The fastest is installed in n and stored for the nest's shape class (log2
  * of the output count and of the reduced size, 128-bit divisibility, body,

@@ -6,7 +6,8 @@
 // that the dynamic tile queue ends with small tiles), device arrays for the
 // nest descriptors, per-output tickets of grid-split nests, tile counters, and
 // two CUDA graphs (upload of the descriptors from one of two pinned host
-// buffers, counter reset, the persistent kernels).  A call refills the pinned
+// buffers, counter reset, the persistent kernels of the arithmetics on parallel
+// branches).  A call refills the pinned
 // buffer the previous-but-one call used (after waiting for that call's event)
 // and replays its graph, so consecutive calls overlap.
 #include <cuda_runtime.h>
@@ -43,6 +44,8 @@ struct BatchCtx {
   };
   std::vector<Group> groups;
   cudaStream_t cap = nullptr;
+  std::vector<cudaStream_t> side;              // capture branches of the second and later arithmetics
+  std::vector<cudaEvent_t> fork_join;          // capture-time dependencies (fork, then one join per branch)
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   cudaEvent_t done[2] = {nullptr, nullptr};
   bool used[2] = {false, false};
@@ -60,6 +63,8 @@ struct BatchCtx {
       if (h_nests[b]) cudaFreeHost(h_nests[b]);
     }
     if (cap) cudaStreamDestroy(cap);
+    for (cudaStream_t st : side) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : fork_join) cudaEventDestroy(ev);
     cudaFree(d_nests);
     cudaFree(d_tiles);
     cudaFree(d_tickets);
@@ -70,6 +75,11 @@ struct BatchCtx {
 std::mutex g_batch_mu;
 std::list<std::unique_ptr<BatchCtx>> g_batch_ctx;   // most recently used first
 constexpr size_t kMaxBatchCtx = 4;
+
+// Can the persistent kernel run this plan?  Its CTA has 8 consumer warps and
+// no cluster: block teams of clusters (or of more warps) run with their own
+// launches instead.
+bool batch_runs(const RectPlan& rp) { return !(rp.team == TEAM_BLOCK && (rp.C > 1 || rp.W > kBatchThreads / 32)); }
 
 hp_status cuda_err(cudaError_t e, const char* what) {
   return fail(HP_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -123,6 +133,7 @@ hp_status build_ctx(BatchCtx& ctx, hp_nest* const* nests, int count, int dev, in
   std::vector<std::vector<int64_t>> per_work(kBatchCombos);
   for (int i = 0; i < count; ++i) {
     const NestPlan& p = nests[i]->plan;
+    if (!batch_runs(p.rp)) continue;   // runs alone, after the persistent kernels
     const int c = batch_combo(p.prec, p.op);
     make_tiles(i, p.rp, target, per[c], per_work[c]);
   }
@@ -156,6 +167,22 @@ hp_status build_ctx(BatchCtx& ctx, hp_nest* const* nests, int count, int dev, in
     return cuda_err(e, "zero tickets");
   if ((e = cudaStreamCreateWithFlags(&ctx.cap, cudaStreamNonBlocking)) != cudaSuccess)
     return cuda_err(e, "capture stream");
+  // the persistent kernels of different arithmetics are independent (own tile
+  // ranges and counters, shared read-only descriptors): they go on parallel
+  // branches of the graph, so the CTAs of one start as the other's drain
+  const size_t n_groups = ctx.groups.size();
+  for (size_t gi = 1; gi < n_groups; ++gi) {
+    cudaStream_t st = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_err(e, "capture branch stream");
+    ctx.side.push_back(st);
+  }
+  for (size_t k = 0; k < n_groups; ++k) {   // [0]: fork, [gi]: join of branch gi
+    cudaEvent_t ev = nullptr;
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_err(e, "capture branch event");
+    ctx.fork_join.push_back(ev);
+  }
   // two graphs: descriptors from pinned buffer b, counters reset, one persistent kernel per arithmetic
   for (int b = 0; b < 2; ++b) {
     if ((e = cudaEventCreateWithFlags(&ctx.done[b], cudaEventDisableTiming)) != cudaSuccess)
@@ -166,11 +193,16 @@ hp_status build_ctx(BatchCtx& ctx, hp_nest* const* nests, int count, int dev, in
                                      cudaMemcpyHostToDevice, ctx.cap);
     if (ce == cudaSuccess)
       ce = cudaMemsetAsync(ctx.d_counters, 0, sizeof(unsigned long long) * kBatchCombos, ctx.cap);
-    for (size_t gi = 0; ce == cudaSuccess && gi < ctx.groups.size(); ++gi) {
+    if (ce == cudaSuccess && n_groups > 1) ce = cudaEventRecord(ctx.fork_join[0], ctx.cap);
+    for (size_t gi = 0; ce == cudaSuccess && gi < n_groups; ++gi) {
       const BatchCtx::Group& g = ctx.groups[gi];
+      cudaStream_t st = gi == 0 ? ctx.cap : ctx.side[gi - 1];
+      if (gi > 0) ce = cudaStreamWaitEvent(st, ctx.fork_join[0], 0);
       BatchLaunch L{ctx.d_nests, ctx.d_tiles + g.first, g.n_tiles, ctx.d_counters + gi, g.grid};
-      ce = launch_batch_combo(g.combo, L, ctx.cap);
+      if (ce == cudaSuccess) ce = launch_batch_combo(g.combo, L, st);
+      if (ce == cudaSuccess && gi > 0) ce = cudaEventRecord(ctx.fork_join[gi], st);
     }
+    for (size_t gi = 1; ce == cudaSuccess && gi < n_groups; ++gi) ce = cudaStreamWaitEvent(ctx.cap, ctx.fork_join[gi], 0);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(ctx.cap, &graph);
     if (ce != cudaSuccess) {
@@ -213,9 +245,6 @@ extern "C" hp_status hp_nest_run_batch(hp_nest* const* nests, const void* const*
     if (n->kind != NEST_RECT) return fail(HP_EUNSUPPORTED, "batched nests must be rectangular");
     const NestPlan& p = n->plan;
     const RectPlan& rp = p.rp;
-    if (rp.team == TEAM_BLOCK && (rp.C > 1 || rp.W > kBatchThreads / 32))
-      return fail(HP_EUNSUPPORTED, "nest " + std::to_string(i) +
-                                       ": batched block teams are single CTAs of at most 8 warps (use hp_nest_run)");
     if (p.body == HP_BODY_GEOMETRIC) return fail(HP_EUNSUPPORTED, "the GEOMETRIC body is not batched");
     hp_status st = ensure_device(n);
     if (st != HP_OK) return st;
@@ -268,6 +297,12 @@ extern "C" hp_status hp_nest_run_batch(hp_nest* const* nests, const void* const*
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if ((e = cudaGraphLaunch(ctx->exec[b], s)) != cudaSuccess) return cuda_err(e, "batch graph launch");
+  // nests the persistent kernel cannot run (cluster teams): their own kernels, same stream
+  for (int i = 0; i < count; ++i) {
+    if (batch_runs(nests[i]->plan.rp)) continue;
+    const hp_status st = run_rect(nests[i], in_dev[i], out_dev[i], s);
+    if (st != HP_OK) return st;
+  }
   if ((e = cudaEventRecord(ctx->done[b], s)) != cudaSuccess) return cuda_err(e, "batch event record");
   ctx->used[b] = true;
   ctx->filled[b] = true;

@@ -43,6 +43,12 @@ constexpr int64_t kCsrChunk = 16384;                      // entries per chunk o
 constexpr int kCsrCtaThreads = 256;
 constexpr int kCsrBinThreads = 256;
 constexpr int kCsrHistSmemMax = 12288;                   // bins counted in shared memory
+#ifndef HP_CSR_GROUPS
+#define HP_CSR_GROUPS 2                                   // 128-bit groups of col / val loaded before their folds
+#endif
+#ifndef HP_CSR_MIN_BLOCKS
+#define HP_CSR_MIN_BLOCKS 1                               // resident CTAs per SM the wide-team kernels' registers allow
+#endif
 
 struct CsrState {
   int64_t* counters = nullptr;   // [0..4] rows per class, [5] chunk slots, [6..10] scatter cursors
@@ -328,8 +334,9 @@ __device__ __forceinline__ void csr_fold_group(const CsrArgs& a, int* sh, const 
 }
 
 // Entries [s, e) for wide teams: the 16-byte-aligned middle is read as 128-bit
-// groups of col and val (lane t takes groups g0 + t, g0 + t + L, ..., two at a
-// time so that 8 gathers of x are in flight), the unaligned head and tail
+// groups of col and val (lane t takes groups g0 + t, g0 + t + L, ...,
+// HP_CSR_GROUPS at a time so that 4 x HP_CSR_GROUPS gathers of x are in
+// flight; the fold order does not depend on it), the unaligned head and tail
 // (< 4 entries each) by lanes 0..3 into their first and second accumulators.
 // The tree depends only on (s, e), so a row's result is reproducible.
 template <class Op, bool HIST>
@@ -348,18 +355,22 @@ __device__ __forceinline__ void csr_fold_vec(const CsrArgs& a, int* sh, int64_t 
   if (t < e - 4 * g1) csr_fold_one<Op, HIST>(a, sh, 4 * g1 + t, acc[1]);
   const int4* col4 = reinterpret_cast<const int4*>(a.col);
   const float4* val4 = reinterpret_cast<const float4*>(a.val);
-  for (int64_t g = g0 + t; g < g1; g += 2 * static_cast<int64_t>(L)) {
-    const bool two = g + L < g1;
-    const int4 c0 = __ldcs(col4 + g);
-    const float4 v0 = __ldcs(val4 + g);
-    int4 c1 = make_int4(0, 0, 0, 0);
-    float4 v1 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (two) {
-      c1 = __ldcs(col4 + g + L);
-      v1 = __ldcs(val4 + g + L);
+  constexpr int K = HP_CSR_GROUPS;
+  for (int64_t g = g0 + t; g < g1; g += K * static_cast<int64_t>(L)) {
+    int4 c[K];
+    float4 v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      c[k] = make_int4(0, 0, 0, 0);
+      v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (g + k * static_cast<int64_t>(L) < g1) {
+        c[k] = __ldcs(col4 + g + k * static_cast<int64_t>(L));
+        v[k] = __ldcs(val4 + g + k * static_cast<int64_t>(L));
+      }
     }
-    csr_fold_group<Op, HIST>(a, sh, c0, v0, acc);
-    if (two) csr_fold_group<Op, HIST>(a, sh, c1, v1, acc);
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if (g + k * static_cast<int64_t>(L) < g1) csr_fold_group<Op, HIST>(a, sh, c[k], v[k], acc);
   }
 }
 
@@ -445,7 +456,7 @@ __device__ __forceinline__ typename Op::Acc cta_fold(const CsrArgs& a, int* sh, 
 
 // class 3: a CTA per row
 template <class Op, bool HIST>
-__global__ void __launch_bounds__(kCsrCtaThreads) csr_cta_kernel(CsrArgs a, const int32_t* __restrict__ rows,
+__global__ void __launch_bounds__(kCsrCtaThreads, HP_CSR_MIN_BLOCKS) csr_cta_kernel(CsrArgs a, const int32_t* __restrict__ rows,
                                                                  const int64_t* counters) {
   extern __shared__ int sh_hist[];
   __shared__ typename Op::Acc wsh[kCsrCtaThreads / 32];
@@ -467,7 +478,7 @@ __global__ void __launch_bounds__(kCsrCtaThreads) csr_cta_kernel(CsrArgs a, cons
 
 // class 4: a CTA per chunk of a long row; the last chunk to finish folds the row
 template <class Op, bool HIST>
-__global__ void __launch_bounds__(kCsrCtaThreads) csr_split_kernel(CsrArgs a, const int64_t* counters,
+__global__ void __launch_bounds__(kCsrCtaThreads, HP_CSR_MIN_BLOCKS) csr_split_kernel(CsrArgs a, const int64_t* counters,
                                                                    const int32_t* __restrict__ chunk_row,
                                                                    const int32_t* __restrict__ chunk_idx,
                                                                    const int32_t* __restrict__ chunk_base,

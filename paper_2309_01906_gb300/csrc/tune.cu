@@ -8,9 +8,13 @@
 // iterations, and the planner's map is kept unless another one is 3% faster.
 //
 // Candidates keep the outputs on the grid and put every reduced level on one
-// hardware level: a CTA of 4 or 8 warps, a warp, a sub-warp group of 2..16
+// hardware level: a CTA of 2 (single runs), 4 or 8 warps, a warp, a sub-warp group of 2..16
 // lanes, the 4 vector slots of one thread, one thread sequentially, or a split
-// of the reduction over several grid parts.  The winner is stored per shape
+// of the reduction over several grid parts.  Long reductions also get cluster
+// teams of 2, 4 or 8 CTAs (single runs only: the batched executor runs single
+// CTAs), and nests with several reduced levels per-level bindings (a CTA's
+// warps over the first reduced level and each warp's lanes over the inner
+// ones; grid parts over the first and a CTA over the rest).  The winner is stored per shape
 // class (log2 of outputs and of the reduced size, 128-bit divisibility, body,
 // precision, operator); nests created later with an automatic map take it.
 #include <cuda_runtime.h>
@@ -28,10 +32,11 @@ hp_status tune_release_device(hp_nest* n);
 
 namespace {
 
-std::vector<TuneChoice> candidates(const NestPlan& p, int sms, bool with_auto) {
+std::vector<TuneChoice> candidates(const NestPlan& p, int sms, bool with_auto, bool batched) {
   int64_t O = 1, R = 1;
   for (int l = 0; l < p.red_level; ++l) O *= p.ext[l];
   for (int l = p.red_level; l < p.depth; ++l) R *= p.ext[l];
+  const int d = p.depth, r = p.red_level;
   std::vector<TuneChoice> c;
   if (with_auto) c.push_back(TuneChoice{});   // the planner's own map first
   auto add = [&](int hw, int sub, int64_t parts) {
@@ -41,12 +46,46 @@ std::vector<TuneChoice> candidates(const NestPlan& p, int sms, bool with_auto) {
     t.split_parts = parts;
     c.push_back(t);
   };
+  // an explicit map: outputs on the grid, the first reduced level on `first`,
+  // the inner reduced levels on `inner` (a per-level binding)
+  auto add_map = [&](hp_level_map first, hp_level_map inner) {
+    TuneChoice t;
+    t.n_map = d;
+    for (int l = 0; l < d; ++l) t.map[l] = l < r ? hp_level_map{HP_HW_GRID, 0, 0} : l == r ? first : inner;
+    c.push_back(t);
+  };
+  if (!batched && R >= 8192) {
+    // cluster teams (DSMEM combine): the batched executor runs single CTAs only
+    for (int C : {2, 4, 8}) {
+      if (R / C < 2048) continue;
+      if (d - r >= 2) {
+        for (int W : {4, 8})
+          if (R / (static_cast<int64_t>(C) * W * 32) >= 8) add_map({HP_HW_CLUSTER, C, 0}, {HP_HW_CTA, W, 0});
+      } else {
+        add_map({HP_HW_CLUSTER, C, 0}, {HP_HW_CLUSTER, C, 0});
+      }
+    }
+  }
+  if (d - r >= 2 && R >= 1024) {
+    // mixed per-level bindings: the warps of a CTA over the first reduced
+    // level, the lanes of each warp over the inner ones
+    for (int W : {4, 8}) add_map({HP_HW_CTA, W, 0}, {HP_HW_WARP, 0, 0});
+    if (R >= 65536 && O < 8 * sms) {
+      // the first reduced level split over grid parts, a CTA over the rest
+      const int64_t n0 = p.ext[r];
+      const int64_t parts = std::max<int64_t>(2, (2 * static_cast<int64_t>(sms) + O - 1) / std::max<int64_t>(O, 1));
+      if (n0 >= 2 * parts) add_map({HP_HW_GRID, 0, (n0 + parts - 1) / parts}, {HP_HW_CTA, 8, 0});
+    }
+  }
   if (R <= 64) add(HP_HW_SEQ, 0, 0);
   if (R % 4 == 0 && R <= 256) add(HP_HW_LANE, 4, 0);
   for (int w : {2, 4, 8, 16})
     if (R >= 2 * w && R <= 256 * w) add(HP_HW_SUBWARP, w, 0);
   if (R >= 32) add(HP_HW_WARP, 0, 0);
   if (R >= 512) {
+    // a CTA of 2 warps puts one short output on more SMs at once (single runs:
+    // in the batched executor it would leave 6 of its 8 consumer warps idle)
+    if (!batched) add(HP_HW_CTA, 2, 0);
     add(HP_HW_CTA, 4, 0);
     add(HP_HW_CTA, 8, 0);
   }
@@ -151,7 +190,7 @@ hp_status tune_impl(hp_nest* n, const hp_level_req* req, const void* const* in_d
     hp_level_map m[HP_MAX_DEPTH];
     any = hp_level_select(p.depth, req, m) == HP_OK;
     std::string why;
-    for (const TuneChoice& c : candidates(p, n->sms > 0 ? n->sms : 152, true)) {   // GB300 before the first run
+    for (const TuneChoice& c : candidates(p, n->sms > 0 ? n->sms : 152, true, false)) {   // GB300 before the first run
       if (any) break;
       tune_apply(p, c, m);
       any = map_meets(p.depth, req, m, &why);
@@ -173,7 +212,7 @@ hp_status tune_impl(hp_nest* n, const hp_level_req* req, const void* const* in_d
   if (!have) {
     float best_ms = FLT_MAX;
     float auto_ms = -1.0f;
-    std::vector<TuneChoice> cand = candidates(p, n->sms, batched || req);
+    std::vector<TuneChoice> cand = candidates(p, n->sms, batched || req, batched);
     if (req) {
       // Sec. 3.2: the requirements are the constraint language; only maps that
       // meet them are timed, and the map chosen from them comes first

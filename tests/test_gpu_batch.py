@@ -109,13 +109,31 @@ def test_uneven_shapes_batch():
         it["nest"].close()
 
 
-def test_batch_rejects_cluster_teams():
-    n = hb.Nest([3, 7, 16, 132], 2, "sum", "f32", "load",
-                level_map=[("grid", 0, 0), ("grid", 0, 0), ("cluster", 4, 0), ("cta", 4, 0)])
-    with pytest.raises(hb.HPError) as e:
-        hb.hp_nest_run_batch([n.handle], [[0x1000]], [0x1000], 0)
-    assert e.value.status == hb.HP_EUNSUPPORTED
-    n.close()
+def test_batch_runs_cluster_teams_alone():
+    # a cluster-team plan cannot run in the persistent kernel's single CTAs:
+    # the batch runs it with its own launch, beside the batched nests, and
+    # every output still equals hp_nest_run's
+    import torch
+    rng = np.random.Generator(np.random.PCG64(407))
+    cases = [([3, 7, 16, 132], 2, "sum", "f32", "load", [("grid", 0, 0), ("grid", 0, 0), ("cluster", 4, 0), ("cta", 4, 0)]),
+             MIXED[0], MIXED[3],
+             ([2, 5, 16, 512], 2, "sum", "f32_comp", "dot_bcast", [("grid", 0, 0), ("grid", 0, 0), ("cluster", 8, 0), ("cta", 2, 0)])]
+    items = [_make(c, rng) for c in cases]
+    s = torch.cuda.current_stream().cuda_stream
+    outs = [_out(it) for it in items]
+    for _ in range(2):   # built, then replayed
+        hb.hp_nest_run_batch([it["nest"].handle for it in items], [it["ins"] for it in items],
+                             [o.data_ptr() for o in outs], s)
+    torch.cuda.synchronize()
+    for it, o in zip(items, outs):
+        single = _out(it)
+        it["nest"].run(it["ins"], single.data_ptr(), s)
+        torch.cuda.synchronize()
+        assert torch.equal(o[:it["O"]], single[:it["O"]]), it["case"]
+        ext, r, op, prec, body, _ = it["case"]
+        ref = oracle_rect(ext, r, op, prec, body, A=it["A"], w=it["w"])
+        assert_close(o[:it["O"]].cpu().numpy(), ref, prec, op, what=f"batch {it['case']}")
+        it["nest"].close()
 
 
 def test_batch_after_destroy_and_recreate():
