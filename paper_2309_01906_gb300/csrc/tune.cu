@@ -98,16 +98,14 @@ std::vector<TuneChoice> candidates(const NestPlan& p, int sms, bool with_auto, b
   return c;
 }
 
-hp_status time_plan(hp_nest* tmp, const void* const* in_dev, void* out_dev, cudaStream_t st, float* ms) {
-  hp_status s = ensure_device(tmp);
-  if (s != HP_OK) return s;
-  if ((s = run_rect(tmp, in_dev, out_dev, st)) != HP_OK) return s;  // warm-up (and launch configuration)
+// mean time of `reps` back-to-back runs between two events
+hp_status time_runs(hp_nest* tmp, const void* const* in_dev, void* out_dev, cudaStream_t st, int reps, float* ms) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  constexpr int kReps = 3;
+  hp_status s = HP_OK;
   cudaEventRecord(e0, st);
-  for (int i = 0; i < kReps && s == HP_OK; ++i) s = run_rect(tmp, in_dev, out_dev, st);
+  for (int i = 0; i < reps && s == HP_OK; ++i) s = run_rect(tmp, in_dev, out_dev, st);
   cudaEventRecord(e1, st);
   const cudaError_t e = cudaEventSynchronize(e1);
   float t = 0.0f;
@@ -116,7 +114,28 @@ hp_status time_plan(hp_nest* tmp, const void* const* in_dev, void* out_dev, cuda
   cudaEventDestroy(e1);
   if (s != HP_OK) return s;
   if (e != cudaSuccess) return fail(HP_ECUDA, std::string("tuning run: ") + cudaGetErrorString(e));
-  *ms = t / kReps;
+  *ms = t / reps;
+  return HP_OK;
+}
+
+// Time one candidate: a warm-up run (it also sizes the launch), then three
+// trials, the best kept.  Each trial runs back to back enough times for about
+// 0.3 ms of device time (3 to 256 runs), so that microsecond kernels are timed
+// on the device rather than by the host's launch rate or the event resolution.
+hp_status time_plan(hp_nest* tmp, const void* const* in_dev, void* out_dev, cudaStream_t st, float* ms) {
+  hp_status s = ensure_device(tmp);
+  if (s != HP_OK) return s;
+  if ((s = run_rect(tmp, in_dev, out_dev, st)) != HP_OK) return s;  // warm-up (and launch configuration)
+  float est = 0.0f;
+  if ((s = time_runs(tmp, in_dev, out_dev, st, 3, &est)) != HP_OK) return s;
+  const int reps = est > 0.0f ? std::max(3, std::min(256, static_cast<int>(0.3f / est))) : 256;
+  float best = FLT_MAX;
+  for (int trial = 0; trial < 3; ++trial) {
+    float t = 0.0f;
+    if ((s = time_runs(tmp, in_dev, out_dev, st, reps, &t)) != HP_OK) return s;
+    best = std::min(best, t);
+  }
+  *ms = best;
   return HP_OK;
 }
 
