@@ -9,11 +9,10 @@
 //   class 1  len <= 32     a group of 8 lanes per row     (SUBWARP(8))
 //   class 2  len <= 1024   a warp per row                 (WARP)
 //   class 3  len <= 16384  a CTA of 256 threads per row   (CTA)
-//   class 4  longer        chunks of 16384 entries, a CTA per chunk; the CTA
-//                          that finishes a row's last chunk folds the chunk
-//                          partials in chunk order (GRID, two-pass; FP64 for
-//                          compensated sums), signalled by a per-row ticket
-//                          (atomic counter, no waiting).
+//   class 4  longer        chunks of 16384 entries, a CTA per chunk writing
+//                          its partial to the chunk's slot; a second kernel
+//                          folds each row's partials in chunk order (GRID,
+//                          two-pass; FP64 for compensated sums).
 // Within a class, lane t of a row's team folds entries start + t + k*L (L the
 // team's lanes) into 4 accumulators (k mod 4), then the team combines them in
 // a fixed tree; the tree depends on the row's length only, never on which
@@ -47,7 +46,7 @@ constexpr int kCsrHistSmemMax = 12288;                   // bins counted in shar
 #define HP_CSR_GROUPS 2                                   // 128-bit groups of col / val loaded before their folds
 #endif
 #ifndef HP_CSR_MIN_BLOCKS
-#define HP_CSR_MIN_BLOCKS 1                               // resident CTAs per SM the wide-team kernels' registers allow
+#define HP_CSR_MIN_BLOCKS 5                               // resident CTAs per SM the wide-team kernels' registers allow (48 registers)
 #endif
 
 struct CsrState {
@@ -55,9 +54,7 @@ struct CsrState {
   int32_t* rows = nullptr;       // row ids grouped by class
   int32_t* chunk_row = nullptr;  // per chunk slot: row id
   int32_t* chunk_idx = nullptr;  // per chunk slot: chunk index within its row
-  int32_t* chunk_base = nullptr; // per chunk slot: first slot of its row
   int32_t* chunk_cnt = nullptr;  // per chunk slot: chunks of its row
-  int32_t* tickets = nullptr;    // per chunk slot (only the row's first slot is used)
   void* part = nullptr;          // per chunk slot: partial accumulator
   int64_t max_chunks = 0;
   int grid_rows = 0;             // persistent grid sizes
@@ -181,7 +178,7 @@ __global__ void csr_bin_count_kernel(const int64_t* __restrict__ off, int64_t n_
 // tile's range); reserve chunk slots of long rows
 __global__ void __launch_bounds__(kCsrBinThreads) csr_bin_scatter_kernel(
     const int64_t* __restrict__ off, int64_t n_rows, int fixed, int64_t* counters, int32_t* rows, int32_t* chunk_row,
-    int32_t* chunk_idx, int32_t* chunk_base, int32_t* chunk_cnt, int64_t max_chunks, int32_t* err) {
+    int32_t* chunk_idx, int32_t* chunk_cnt, int64_t max_chunks, int32_t* err) {
   constexpr int kWarps = kCsrBinThreads / 32;
   __shared__ int wpos[kWarps][kCsrClasses];
   __shared__ long long bbase[kCsrClasses];
@@ -236,7 +233,6 @@ __global__ void __launch_bounds__(kCsrBinThreads) csr_bin_scatter_kernel(
         for (int64_t k = 0; k < nc; ++k) {
           chunk_row[base + k] = static_cast<int32_t>(i);
           chunk_idx[base + k] = static_cast<int32_t>(k);
-          chunk_base[base + k] = static_cast<int32_t>(base);
           chunk_cnt[base + k] = static_cast<int32_t>(nc);
         }
       }
@@ -434,7 +430,10 @@ __global__ void __launch_bounds__(256) csr_rows_kernel(CsrArgs a, const int32_t*
   }
 }
 
-// CTA-wide fold of one entry range; the result is valid in thread 0
+// CTA-wide fold of one entry range; the result is valid in thread 0.  One
+// barrier: callers alternate between the two halves of their warp-partial
+// buffer, so that the next range's partials never overwrite the ones thread 0
+// may still be reading.
 template <class Op, bool HIST>
 __device__ __forceinline__ typename Op::Acc cta_fold(const CsrArgs& a, int* sh, int64_t s, int64_t e,
                                                      typename Op::Acc* wsh) {
@@ -450,7 +449,6 @@ __device__ __forceinline__ typename Op::Acc cta_fold(const CsrArgs& a, int* sh, 
     r = wsh[0];
     for (int w = 1; w < nw; ++w) r = Op::combine(r, wsh[w]);
   }
-  __syncthreads();
   return r;
 }
 
@@ -459,16 +457,17 @@ template <class Op, bool HIST>
 __global__ void __launch_bounds__(kCsrCtaThreads, HP_CSR_MIN_BLOCKS) csr_cta_kernel(CsrArgs a, const int32_t* __restrict__ rows,
                                                                  const int64_t* counters) {
   extern __shared__ int sh_hist[];
-  __shared__ typename Op::Acc wsh[kCsrCtaThreads / 32];
+  __shared__ typename Op::Acc wsh[2][kCsrCtaThreads / 32];
   if constexpr (HIST) {
     if (a.smem_bins) hist_init(sh_hist, a.smem_bins);
   }
   int64_t start = 0;
   for (int c = 0; c < 3; ++c) start += counters[c];
   const int64_t count = counters[3];
-  for (int64_t k = blockIdx.x; k < count; k += gridDim.x) {
+  int buf = 0;
+  for (int64_t k = blockIdx.x; k < count; k += gridDim.x, buf ^= 1) {
     const int32_t row = rows[start + k];
-    const typename Op::Acc r = cta_fold<Op, HIST>(a, sh_hist, a.off[row], a.off[row + 1], wsh);
+    const typename Op::Acc r = cta_fold<Op, HIST>(a, sh_hist, a.off[row], a.off[row + 1], wsh[buf]);
     if (threadIdx.x == 0) a.y[row] = Op::finish(r);
   }
   if constexpr (HIST) {
@@ -476,56 +475,61 @@ __global__ void __launch_bounds__(kCsrCtaThreads, HP_CSR_MIN_BLOCKS) csr_cta_ker
   }
 }
 
-// class 4: a CTA per chunk of a long row; the last chunk to finish folds the row
+// class 4: a CTA per chunk of a long row; each chunk's partial goes to its
+// slot, and csr_split_combine_kernel folds a row's slots after this kernel
 template <class Op, bool HIST>
 __global__ void __launch_bounds__(kCsrCtaThreads, HP_CSR_MIN_BLOCKS) csr_split_kernel(CsrArgs a, const int64_t* counters,
                                                                    const int32_t* __restrict__ chunk_row,
                                                                    const int32_t* __restrict__ chunk_idx,
-                                                                   const int32_t* __restrict__ chunk_base,
-                                                                   const int32_t* __restrict__ chunk_cnt,
-                                                                   int32_t* tickets, typename Op::Acc* part,
-                                                                   int64_t max_chunks) {
+                                                                   typename Op::Acc* part, int64_t max_chunks) {
   extern __shared__ int sh_hist[];
-  __shared__ typename Op::Acc wsh[kCsrCtaThreads / 32];
-  __shared__ int last;
+  __shared__ typename Op::Acc wsh[2][kCsrCtaThreads / 32];
   if constexpr (HIST) {
     if (a.smem_bins) hist_init(sh_hist, a.smem_bins);
   }
   const int64_t n_slots = counters[11] < max_chunks ? counters[11] : max_chunks;
-  for (int64_t k = blockIdx.x; k < n_slots; k += gridDim.x) {
+  int buf = 0;
+  for (int64_t k = blockIdx.x; k < n_slots; k += gridDim.x, buf ^= 1) {
     const int32_t row = chunk_row[k];
     const int64_t c = chunk_idx[k];
     const int64_t s = a.off[row] + c * kCsrChunk;
     const int64_t e0 = a.off[row + 1];
     const int64_t e = (s + kCsrChunk < e0) ? s + kCsrChunk : e0;
-    const typename Op::Acc r = cta_fold<Op, HIST>(a, sh_hist, s, e, wsh);
-    if (threadIdx.x == 0) {
-      part[k] = r;
-      __threadfence();   // publish the partial before taking a ticket
-      const int base = chunk_base[k], n = chunk_cnt[k];
-      last = (atomicAdd(&tickets[base], 1) == n - 1) ? 1 : 0;
-      if (last) {
-        __threadfence();  // every other chunk's partial is visible
-        if constexpr (sizeof(typename Op::Acc) == 8 && Op::kFp) {
-          double sum = 0.0;
-          for (int q = 0; q < n; ++q) {
-            const volatile float* pv = reinterpret_cast<const volatile float*>(part) + 2 * (base + q);
-            sum += static_cast<double>(pv[0]);
-            sum += static_cast<double>(pv[1]);
-          }
-          a.y[row] = static_cast<float>(sum);
-        } else {
-          typename Op::Acc v = *reinterpret_cast<volatile typename Op::Acc*>(part + base);
-          for (int q = 1; q < n; ++q) v = Op::combine(v, *reinterpret_cast<volatile typename Op::Acc*>(part + base + q));
-          a.y[row] = Op::finish(v);
-        }
-        tickets[base] = 0;  // ready for the next run
-      }
-    }
-    __syncthreads();
+    const typename Op::Acc r = cta_fold<Op, HIST>(a, sh_hist, s, e, wsh[buf]);
+    if (threadIdx.x == 0) part[k] = r;
   }
   if constexpr (HIST) {
     if (a.smem_bins) hist_flush(a, sh_hist);
+  }
+}
+
+// the second pass of long rows (Sec. 2's recursive reduction at grid level):
+// the thread of a row's first slot folds the row's chunk partials in chunk
+// order (FP64 for compensated sums, rounded once), a fixed tree per row
+template <class Op>
+__global__ void csr_split_combine_kernel(float* __restrict__ y, const int64_t* counters,
+                                         const int32_t* __restrict__ chunk_row, const int32_t* __restrict__ chunk_idx,
+                                         const int32_t* __restrict__ chunk_cnt, const typename Op::Acc* __restrict__ part,
+                                         int64_t max_chunks) {
+  const int64_t n_slots = counters[11] < max_chunks ? counters[11] : max_chunks;
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < n_slots;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    if (chunk_idx[k] != 0) continue;
+    const int n = chunk_cnt[k];
+    if (n < 1 || k + n > n_slots) continue;   // a row the binning could not place whole (flagged there)
+    if constexpr (sizeof(typename Op::Acc) == 8 && Op::kFp) {
+      double sum = 0.0;
+      for (int q = 0; q < n; ++q) {
+        const f2 v = part[k + q];
+        sum += static_cast<double>(v.s);
+        sum += static_cast<double>(v.c);
+      }
+      y[chunk_row[k]] = static_cast<float>(sum);
+    } else {
+      typename Op::Acc v = part[k];
+      for (int q = 1; q < n; ++q) v = Op::combine(v, part[k + q]);
+      y[chunk_row[k]] = Op::finish(v);
+    }
   }
 }
 
@@ -585,10 +589,13 @@ hp_status launch_classes(hp_nest* n, const CsrArgs& a, cudaStream_t st) {
   if (fixed < 0 || fixed == 1) csr_rows_kernel<Op, 8, HIST><<<cs.grid_rows, 256, dyn, st>>>(a, cs.rows, cs.counters, 1);
   if (fixed < 0 || fixed == 2) csr_rows_kernel<Op, 32, HIST><<<cs.grid_rows, 256, dyn, st>>>(a, cs.rows, cs.counters, 2);
   if (fixed < 0 || fixed == 3) csr_cta_kernel<Op, HIST><<<cs.grid_cta, kCsrCtaThreads, dyn, st>>>(a, cs.rows, cs.counters);
-  if (fixed < 0 || fixed == 4)
+  if (fixed < 0 || fixed == 4) {
     csr_split_kernel<Op, HIST><<<cs.grid_cta, kCsrCtaThreads, dyn, st>>>(
-        a, cs.counters, cs.chunk_row, cs.chunk_idx, cs.chunk_base, cs.chunk_cnt, cs.tickets,
-        static_cast<typename Op::Acc*>(cs.part), cs.max_chunks);
+        a, cs.counters, cs.chunk_row, cs.chunk_idx, static_cast<typename Op::Acc*>(cs.part), cs.max_chunks);
+    const int cgrid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((cs.max_chunks + 255) / 256, 4 * n->sms)));
+    csr_split_combine_kernel<Op><<<cgrid, 256, 0, st>>>(a.y, cs.counters, cs.chunk_row, cs.chunk_idx, cs.chunk_cnt,
+                                                        static_cast<const typename Op::Acc*>(cs.part), cs.max_chunks);
+  }
   const cudaError_t e = cudaPeekAtLastError();
   return e == cudaSuccess ? HP_OK : cuda_fail(e, "CSR class kernel launch");
 }
@@ -621,14 +628,12 @@ hp_status csr_prepare(hp_nest* n) {
   const size_t mc = static_cast<size_t>(cs->max_chunks);
   if (cudaMalloc(&cs->chunk_row, mc * sizeof(int32_t)) != cudaSuccess ||
       cudaMalloc(&cs->chunk_idx, mc * sizeof(int32_t)) != cudaSuccess ||
-      cudaMalloc(&cs->chunk_base, mc * sizeof(int32_t)) != cudaSuccess ||
       cudaMalloc(&cs->chunk_cnt, mc * sizeof(int32_t)) != cudaSuccess ||
-      cudaMalloc(&cs->tickets, mc * sizeof(int32_t)) != cudaSuccess ||
       cudaMalloc(&cs->part, mc * sizeof(f2)) != cudaSuccess)
     return fail(HP_ENOMEM, "cudaMalloc (CSR chunk tables)");
   // every slot starts as a valid (row 0, chunk 0) entry, so a slot the binning
   // could not fill (offsets beyond the declared nnz, flagged) reads in bounds
-  for (int32_t* t : {cs->tickets, cs->chunk_row, cs->chunk_idx, cs->chunk_base, cs->chunk_cnt}) {
+  for (int32_t* t : {cs->chunk_row, cs->chunk_idx, cs->chunk_cnt}) {
     e = cudaMemset(t, 0, mc * sizeof(int32_t));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemset (chunk tables)");
   }
@@ -696,7 +701,7 @@ hp_status run_csr(hp_nest* n, const void* const* in_dev, void* out_dev, cudaStre
                                                                            8 * n->sms)));
   csr_bin_count_kernel<<<bgrid, kCsrBinThreads, 0, st>>>(a.off, p.n_rows, p.fixed_class, cs.counters);
   csr_bin_scatter_kernel<<<bgrid, kCsrBinThreads, 0, st>>>(a.off, p.n_rows, p.fixed_class, cs.counters, cs.rows,
-                                                          cs.chunk_row, cs.chunk_idx, cs.chunk_base, cs.chunk_cnt,
+                                                          cs.chunk_row, cs.chunk_idx, cs.chunk_cnt,
                                                           cs.max_chunks, n->err);
   cudaError_t e = cudaPeekAtLastError();
   if (e != cudaSuccess) return cuda_fail(e, "CSR binning launch");
@@ -773,9 +778,7 @@ void csr_release(hp_nest* n) {
   cudaFree(cs->rows);
   cudaFree(cs->chunk_row);
   cudaFree(cs->chunk_idx);
-  cudaFree(cs->chunk_base);
   cudaFree(cs->chunk_cnt);
-  cudaFree(cs->tickets);
   cudaFree(cs->part);
   delete cs;
   n->cs = nullptr;
