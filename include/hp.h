@@ -591,6 +591,8 @@ void hp_stencil_destroy(hp_stencil *s);
  *               Both give bit-identical results (same reduction tree).
  *   "serve_batching"  1 (default): servers pack admitted requests into
  *               batched steps; 0: servers launch each request alone.
+ *   "tune_log"  0 (default); 1: hp_nest_tune* write every candidate's map,
+ *               kernel and time to stderr.
  * HP_EINVAL for an unknown name.
  */
 hp_status hp_set_option(const char *name, int64_t value);

@@ -162,6 +162,10 @@ hp_status hp_set_option(const char* name, int64_t value) {
     options().serve_batching = value;
     return HP_OK;
   }
+  if (n == "tune_log") {
+    options().tune_log = value;
+    return HP_OK;
+  }
   return fail(HP_EINVAL, "unknown option " + n);
 }
 
@@ -174,6 +178,10 @@ hp_status hp_get_option(const char* name, int64_t* value) {
   }
   if (n == "serve_batching") {
     *value = options().serve_batching;
+    return HP_OK;
+  }
+  if (n == "tune_log") {
+    *value = options().tune_log;
     return HP_OK;
   }
   return fail(HP_EINVAL, "unknown option " + n);

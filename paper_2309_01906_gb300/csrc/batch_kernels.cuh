@@ -668,7 +668,8 @@ __device__ __forceinline__ void ring_lanes_items(const RingGeom& gm, const Fold&
           if (jb < n) fold.template run_pair<V>(offA, dist, s0, R, gm.P, accA, accB);
           else if (ja < n) fold.template run_at<V>(offA, fold.w, s0, R, gm.P, accA);
           const Acc a = lanes_allreduce<Op>(fold_vec<Op, V>(accA), L);
-          const Acc c = lanes_allreduce<Op>(fold_vec<Op, V>(accB), L);
+          // a thread team (L = 1) has no partner to shuffle with: skip the empty second item
+          const Acc c = (L == 1 && jb >= n) ? Op::ident() : lanes_allreduce<Op>(fold_vec<Op, V>(accB), L);
           if (lt == 0) {
             if (ja < n) outp[b + ja] = Op::finish(a);
             if (jb < n) outp[b + jb] = Op::finish(c);

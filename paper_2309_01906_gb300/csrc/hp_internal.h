@@ -176,6 +176,7 @@ double error_bound_rect(const NestPlan& p);
 struct Options {
   int64_t pipeline = 1;    // allow the cp.async-pipelined block kernel
   int64_t serve_batching = 1;  // servers created now pack admitted requests into batched steps
+  int64_t tune_log = 0;    // the tuner writes each candidate's map and time to stderr
 };
 Options& options();
 

@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <cfloat>
+#include <cstdio>
 #include <string>
 #include <vector>
 
@@ -29,6 +30,7 @@
 namespace hp {
 
 hp_status tune_release_device(hp_nest* n);
+const std::string& last_error_string();
 
 namespace {
 
@@ -272,6 +274,14 @@ hp_status tune_impl(hp_nest* n, const hp_level_req* req, const void* const* in_d
       float ms = 0.0f;
       const hp_status ts = batched ? time_plan_batched(tmp, in_dev, out_dev, st, copies, &ms)
                                    : time_plan(tmp, in_dev, out_dev, st, &ms);
+      if (options().tune_log) {
+        std::string mp;
+        for (int l = 0; l < p.depth; ++l)
+          mp += std::string(l ? "," : "") + std::to_string(m[l].hw) + ":" + std::to_string(m[l].sub_width) + ":" +
+                std::to_string(m[l].tile);
+        std::fprintf(stderr, "hp tune: map [%s] %s %.4f ms%s\n", mp.c_str(), tmp->plan.kernel.c_str(), ms,
+                     ts == HP_OK ? "" : (" failed: " + last_error_string()).c_str());
+      }
       hp_nest_destroy(tmp);
       if (ts != HP_OK) {
         if (ts == HP_ECUDA) return ts;
