@@ -328,7 +328,9 @@ hp_status hp_nest_run_batch(hp_nest *const *nests, const void *const *const *in_
  * CTAs and the inner ones to a CTA (not in batched timing), or, with several
  * reduced levels, the first to the warps of a CTA (or to grid parts) and the
  * inner ones to the lanes of each warp (or to a CTA);
- * each is run on in_dev / out_dev on `stream` and timed with CUDA events.
+ * each is run on in_dev / out_dev, once on `stream`, then (after `stream`
+ * is synchronized) as a CUDA graph of back-to-back runs on a private stream,
+ * timed with CUDA events, best of three (device time, not launch rate).
  * The fastest is installed in n and stored for the nest's shape class (log2
  * of the output count and of the reduced size, 128-bit divisibility, body,
  * precision, operator); nests created later with map == NULL take it.

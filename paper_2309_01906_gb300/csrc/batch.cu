@@ -3,8 +3,7 @@
 //
 // Per distinct list of nests a context is built once: a tile table (each
 // nest's work items cut into tiles of similar size, ordered largest first so
-// that the dynamic tile queue ends with small tiles, CTA-team and lanes-team
-// tiles interleaved by work), device arrays for the
+// that the dynamic tile queue ends with small tiles), device arrays for the
 // nest descriptors, per-output tickets of grid-split nests, tile counters, and
 // two CUDA graphs (upload of the descriptors from one of two pinned host
 // buffers, counter reset, the persistent kernels of the arithmetics on parallel
@@ -108,40 +107,6 @@ void make_tiles(int nest, const RectPlan& rp, int64_t target, std::vector<BatchT
   }
 }
 
-// Order of one arithmetic's tiles in its queue.  Tiles of CTA teams stream
-// at close to the copy rate, while tiles of lanes teams (warps, sub-warp
-// groups, threads) spend more issue slots per byte; both kinds are taken
-// largest first (LPT: the queue ends with small tiles), and the two lists are
-// merged so that each has consumed about the same fraction of its work at
-// every point, which keeps both kinds of work side by side on the SMs until
-// the end instead of leaving the issue-bound kind for last.
-std::vector<size_t> interleaved_order(const std::vector<BatchTile>& tiles, const std::vector<int64_t>& work,
-                                      hp_nest* const* nests) {
-  std::vector<size_t> kind[2];
-  double total[2] = {0.0, 0.0};
-  for (size_t i = 0; i < tiles.size(); ++i) {
-    const int k = nests[tiles[i].nest]->plan.rp.team == TEAM_BLOCK ? 0 : 1;
-    kind[k].push_back(i);
-    total[k] += static_cast<double>(work[i]);
-  }
-  for (auto& v : kind)
-    std::stable_sort(v.begin(), v.end(), [&](size_t a, size_t b) { return work[a] > work[b]; });
-  std::vector<size_t> out;
-  out.reserve(tiles.size());
-  size_t pos[2] = {0, 0};
-  double done[2] = {0.0, 0.0};
-  while (pos[0] < kind[0].size() || pos[1] < kind[1].size()) {
-    int k;
-    if (pos[0] == kind[0].size()) k = 1;
-    else if (pos[1] == kind[1].size()) k = 0;
-    else k = (done[0] / total[0] <= done[1] / total[1]) ? 0 : 1;
-    const size_t i = kind[k][pos[k]++];
-    done[k] += static_cast<double>(work[i]);
-    out.push_back(i);
-  }
-  return out;
-}
-
 hp_status build_ctx(BatchCtx& ctx, hp_nest* const* nests, int count, int dev, int sms) {
   ctx.device = dev;
   cudaError_t e;
@@ -175,7 +140,9 @@ hp_status build_ctx(BatchCtx& ctx, hp_nest* const* nests, int count, int dev, in
   std::vector<BatchTile> all;
   for (int c = 0; c < kBatchCombos; ++c) {
     if (per[c].empty()) continue;
-    std::vector<size_t> idx = interleaved_order(per[c], per_work[c], nests);
+    std::vector<size_t> idx(per[c].size());
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return per_work[c][a] > per_work[c][b]; });
     BatchCtx::Group g;
     g.combo = c;
     g.first = static_cast<int64_t>(all.size());

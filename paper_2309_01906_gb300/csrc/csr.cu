@@ -256,23 +256,11 @@ struct CsrArgs {
   int smem_bins;        // bins counted in shared memory (0: count straight into global memory)
 };
 
-#ifndef HP_CSR_HIST_RED
-#define HP_CSR_HIST_RED 0
-#endif
 __device__ __forceinline__ void hist_add(const CsrArgs& a, int* sh, int32_t c) {
   const int64_t b = static_cast<int64_t>(c) >> a.shift;
   if (b < a.n_bins) {
-    if (a.smem_bins) {
-#if HP_CSR_HIST_RED
-      // a reduction without a returned value: nothing waits for it
-      asm volatile("red.shared.add.u32 [%0], 1;\n" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(sh + b)))
-                   : "memory");
-#else
-      atomicAdd(&sh[b], 1);
-#endif
-    } else {
-      atomicAdd(reinterpret_cast<unsigned long long*>(&a.hist[b]), 1ull);
-    }
+    if (a.smem_bins) atomicAdd(&sh[b], 1);
+    else atomicAdd(reinterpret_cast<unsigned long long*>(&a.hist[b]), 1ull);
   }
 }
 

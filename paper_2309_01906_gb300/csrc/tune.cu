@@ -120,23 +120,68 @@ hp_status time_runs(hp_nest* tmp, const void* const* in_dev, void* out_dev, cuda
   return HP_OK;
 }
 
-// Time one candidate: a warm-up run (it also sizes the launch), then three
-// trials, the best kept.  Each trial runs back to back enough times for about
-// 0.3 ms of device time (3 to 256 runs), so that microsecond kernels are timed
-// on the device rather than by the host's launch rate or the event resolution.
+// mean device time of `reps` runs captured back to back in one CUDA graph on
+// the private stream cs (the host's launch rate does not enter)
+hp_status time_runs_graph(hp_nest* tmp, const void* const* in_dev, void* out_dev, cudaStream_t cs, int reps,
+                          float* ms) {
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return fail(HP_ECUDA, std::string("tuning capture: ") + cudaGetErrorString(e));
+  hp_status s = HP_OK;
+  for (int i = 0; i < reps && s == HP_OK; ++i) s = run_rect(tmp, in_dev, out_dev, cs);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(cs, &g);
+  if (s != HP_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return s != HP_OK ? s : fail(HP_ECUDA, std::string("tuning capture: ") + cudaGetErrorString(e));
+  }
+  cudaGraphExec_t x = nullptr;
+  e = cudaGraphInstantiate(&x, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(HP_ECUDA, std::string("tuning graph: ") + cudaGetErrorString(e));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  e = cudaGraphLaunch(x, cs);   // warm
+  cudaEventRecord(e0, cs);
+  if (e == cudaSuccess) e = cudaGraphLaunch(x, cs);
+  cudaEventRecord(e1, cs);
+  const cudaError_t es = cudaEventSynchronize(e1);
+  float t = 0.0f;
+  if (e == cudaSuccess && es == cudaSuccess) cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGraphExecDestroy(x);
+  if (e != cudaSuccess || es != cudaSuccess)
+    return fail(HP_ECUDA, std::string("tuning run: ") + cudaGetErrorString(e != cudaSuccess ? e : es));
+  *ms = t / reps;
+  return HP_OK;
+}
+
+// Time one candidate: a warm-up run on the caller's stream (it also sizes the
+// launch), then three trials, the best kept.  A trial replays a CUDA graph of
+// enough back-to-back runs for about 0.3 ms of device time (3 to 256 runs), so
+// that microsecond kernels are timed on the device, not by the host's launch
+// rate or the event resolution.
 hp_status time_plan(hp_nest* tmp, const void* const* in_dev, void* out_dev, cudaStream_t st, float* ms) {
   hp_status s = ensure_device(tmp);
   if (s != HP_OK) return s;
   if ((s = run_rect(tmp, in_dev, out_dev, st)) != HP_OK) return s;  // warm-up (and launch configuration)
   float est = 0.0f;
   if ((s = time_runs(tmp, in_dev, out_dev, st, 3, &est)) != HP_OK) return s;
+  cudaError_t e = cudaStreamSynchronize(st);   // the capture stream takes over the caller's buffers
+  if (e != cudaSuccess) return fail(HP_ECUDA, std::string("tuning: ") + cudaGetErrorString(e));
+  cudaStream_t cs = nullptr;
+  e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return fail(HP_ECUDA, std::string("tuning stream: ") + cudaGetErrorString(e));
   const int reps = est > 0.0f ? std::max(3, std::min(256, static_cast<int>(0.3f / est))) : 256;
   float best = FLT_MAX;
-  for (int trial = 0; trial < 3; ++trial) {
+  for (int trial = 0; trial < 3 && s == HP_OK; ++trial) {
     float t = 0.0f;
-    if ((s = time_runs(tmp, in_dev, out_dev, st, reps, &t)) != HP_OK) return s;
+    s = time_runs_graph(tmp, in_dev, out_dev, cs, reps, &t);
     best = std::min(best, t);
   }
+  cudaStreamDestroy(cs);
+  if (s != HP_OK) return s;
   *ms = best;
   return HP_OK;
 }
