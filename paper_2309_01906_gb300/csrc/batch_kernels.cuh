@@ -37,10 +37,10 @@ constexpr int kBatchThreads = 256;                       // consumer threads: bl
 constexpr int kBatchWarps = kBatchThreads / 32;
 constexpr int kBatchAllThreads = kBatchThreads + 32;     // + the producer warp
 #ifndef HP_BATCH_STAGE_BYTES
-#define HP_BATCH_STAGE_BYTES 8192
+#define HP_BATCH_STAGE_BYTES 16384
 #endif
 #ifndef HP_BATCH_STAGES
-#define HP_BATCH_STAGES 8
+#define HP_BATCH_STAGES 4
 #endif
 constexpr int kStageBytes = HP_BATCH_STAGE_BYTES;        // one ring stage
 constexpr int kStages = HP_BATCH_STAGES;
