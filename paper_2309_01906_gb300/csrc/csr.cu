@@ -394,7 +394,7 @@ __device__ __forceinline__ void hist_flush(const CsrArgs& a, int* sh) {
 
 // classes 0..2: a team of L lanes (1, 8 or 32) per row; persistent over the class list
 template <class Op, int L, bool HIST>
-__global__ void __launch_bounds__(256) csr_rows_kernel(CsrArgs a, const int32_t* __restrict__ rows, const int64_t* counters,
+__global__ void __launch_bounds__(256, HP_CSR_MIN_BLOCKS) csr_rows_kernel(CsrArgs a, const int32_t* __restrict__ rows, const int64_t* counters,
                                                        int cls) {
   extern __shared__ int sh_hist[];
   if constexpr (HIST) {
@@ -408,22 +408,34 @@ __global__ void __launch_bounds__(256) csr_rows_kernel(CsrArgs a, const int32_t*
   const int64_t team = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) / L;
   const int64_t n_teams = static_cast<int64_t>(gridDim.x) * blockDim.x / L;
   const int64_t warp_first_team = (blockIdx.x * static_cast<int64_t>(blockDim.x) + (threadIdx.x & ~31)) / L;
-  // every lane of a warp runs the same number of rounds (shuffles need the whole warp)
-  for (int64_t r0 = warp_first_team; r0 < count; r0 += n_teams) {
-    const int64_t k = r0 + (team - warp_first_team);
+  // every lane of a warp runs the same number of rounds (shuffles need the whole warp);
+  // the row id two rounds ahead and the offsets one round ahead are loaded
+  // before the current round's fold, so that their dependent loads overlap it
+  const int64_t dk = team - warp_first_team;
+  int64_t r0 = warp_first_team;
+  int32_t row = r0 + dk < count ? rows[start + r0 + dk] : 0;
+  int32_t row1 = r0 + n_teams + dk < count ? rows[start + r0 + n_teams + dk] : 0;
+  int64_t s0 = r0 + dk < count ? a.off[row] : 0, e0 = r0 + dk < count ? a.off[row + 1] : 0;
+  for (; r0 < count; r0 += n_teams) {
+    const int64_t k = r0 + dk;
     const bool valid = k < count;
+    const int32_t row2 = k + 2 * n_teams < count ? rows[start + k + 2 * n_teams] : 0;
+    const int64_t s1 = k + n_teams < count ? a.off[row1] : 0;
+    const int64_t e1 = k + n_teams < count ? a.off[row1 + 1] : 0;
     typename Op::Acc acc[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) acc[u] = Op::ident();
-    int32_t row = 0;
     if (valid) {
-      row = rows[start + k];
-      if constexpr (L == 32) csr_fold_vec<Op, HIST>(a, sh_hist, a.off[row], a.off[row + 1], lt, L, acc);
-      else csr_fold<Op, HIST>(a, sh_hist, a.off[row], a.off[row + 1], lt, L, acc);
+      if constexpr (L == 32) csr_fold_vec<Op, HIST>(a, sh_hist, s0, e0, lt, L, acc);
+      else csr_fold<Op, HIST>(a, sh_hist, s0, e0, lt, L, acc);
     }
     typename Op::Acc r = fold4<Op>(acc);
     if constexpr (L > 1) r = team_reduce<Op>(r, L);
     if (valid && lt == 0) a.y[row] = Op::finish(r);
+    row = row1;
+    row1 = row2;
+    s0 = s1;
+    e0 = e1;
   }
   if constexpr (HIST) {
     if (a.smem_bins) hist_flush(a, sh_hist);
@@ -464,11 +476,24 @@ __global__ void __launch_bounds__(kCsrCtaThreads, HP_CSR_MIN_BLOCKS) csr_cta_ker
   int64_t start = 0;
   for (int c = 0; c < 3; ++c) start += counters[c];
   const int64_t count = counters[3];
+  const int64_t G = gridDim.x;
   int buf = 0;
-  for (int64_t k = blockIdx.x; k < count; k += gridDim.x, buf ^= 1) {
-    const int32_t row = rows[start + k];
-    const typename Op::Acc r = cta_fold<Op, HIST>(a, sh_hist, a.off[row], a.off[row + 1], wsh[buf]);
+  // the row id two rows ahead and the offsets one row ahead are loaded before
+  // the current row's fold, so that their dependent loads overlap it
+  int64_t k = blockIdx.x;
+  int32_t row = k < count ? rows[start + k] : 0;
+  int32_t row1 = k + G < count ? rows[start + k + G] : 0;
+  int64_t s0 = k < count ? a.off[row] : 0, e0 = k < count ? a.off[row + 1] : 0;
+  for (; k < count; k += G, buf ^= 1) {
+    const int32_t row2 = k + 2 * G < count ? rows[start + k + 2 * G] : 0;
+    const int64_t s1 = k + G < count ? a.off[row1] : 0;
+    const int64_t e1 = k + G < count ? a.off[row1 + 1] : 0;
+    const typename Op::Acc r = cta_fold<Op, HIST>(a, sh_hist, s0, e0, wsh[buf]);
     if (threadIdx.x == 0) a.y[row] = Op::finish(r);
+    row = row1;
+    row1 = row2;
+    s0 = s1;
+    e0 = e1;
   }
   if constexpr (HIST) {
     if (a.smem_bins) hist_flush(a, sh_hist);
@@ -488,15 +513,38 @@ __global__ void __launch_bounds__(kCsrCtaThreads, HP_CSR_MIN_BLOCKS) csr_split_k
     if (a.smem_bins) hist_init(sh_hist, a.smem_bins);
   }
   const int64_t n_slots = counters[11] < max_chunks ? counters[11] : max_chunks;
+  const int64_t G = gridDim.x;
   int buf = 0;
-  for (int64_t k = blockIdx.x; k < n_slots; k += gridDim.x, buf ^= 1) {
-    const int32_t row = chunk_row[k];
-    const int64_t c = chunk_idx[k];
-    const int64_t s = a.off[row] + c * kCsrChunk;
-    const int64_t e0 = a.off[row + 1];
-    const int64_t e = (s + kCsrChunk < e0) ? s + kCsrChunk : e0;
-    const typename Op::Acc r = cta_fold<Op, HIST>(a, sh_hist, s, e, wsh[buf]);
+  // a chunk's range: [off[row] + c * chunk, min(that + chunk, off[row + 1]))
+  auto range = [&](int32_t row, int32_t c, int64_t& s, int64_t& e) {
+    s = a.off[row] + static_cast<int64_t>(c) * kCsrChunk;
+    const int64_t end = a.off[row + 1];
+    e = (s + kCsrChunk < end) ? s + kCsrChunk : end;
+  };
+  // the slot two chunks ahead and the offsets one chunk ahead are loaded
+  // before the current chunk's fold, so that their dependent loads overlap it
+  int64_t k = blockIdx.x;
+  int32_t row1 = 0, c1 = 0;
+  int64_t s0 = 0, e0 = 0;
+  if (k < n_slots) range(chunk_row[k], chunk_idx[k], s0, e0);
+  if (k + G < n_slots) {
+    row1 = chunk_row[k + G];
+    c1 = chunk_idx[k + G];
+  }
+  for (; k < n_slots; k += G, buf ^= 1) {
+    int32_t row2 = 0, c2 = 0;
+    if (k + 2 * G < n_slots) {
+      row2 = chunk_row[k + 2 * G];
+      c2 = chunk_idx[k + 2 * G];
+    }
+    int64_t s1 = 0, e1 = 0;
+    if (k + G < n_slots) range(row1, c1, s1, e1);
+    const typename Op::Acc r = cta_fold<Op, HIST>(a, sh_hist, s0, e0, wsh[buf]);
     if (threadIdx.x == 0) part[k] = r;
+    row1 = row2;
+    c1 = c2;
+    s0 = s1;
+    e0 = e1;
   }
   if constexpr (HIST) {
     if (a.smem_bins) hist_flush(a, sh_hist);

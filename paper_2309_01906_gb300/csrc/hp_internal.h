@@ -144,8 +144,10 @@ struct NarrowPlan {
 // hardware level, outputs over the grid).
 struct TuneChoice {
   int32_t red_hw = HP_HW_AUTO;  // hardware level of the reduced levels (AUTO: the planner's map)
-  int32_t sub = 0;              // SUBWARP width, LANE vector slots, or CTA warps
+  int32_t sub = 0;              // SUBWARP width, LANE vector slots, CTA warps or cluster CTAs
   int64_t split_parts = 0;      // > 0: reduced levels split over this many grid parts
+  int32_t inner_hw = HP_HW_AUTO;  // reduced levels after the first: their own level (AUTO: as the first)
+  int32_t inner_sub = 0;
   int32_t n_map = 0;            // > 0: this explicit map instead (the map chosen from level requirements)
   hp_level_map map[HP_MAX_DEPTH] = {};
 };

@@ -110,9 +110,16 @@ static void auto_map(const NestPlan& p, hp_level_map* m);
 
 // outputs over the grid; every reduced level on the chosen hardware level
 // (HP_HW_AUTO: the planner's own map)
+// A choice is structural (the hardware of the first reduced level and of the
+// inner ones), so that a shape class's choice applies to every nest of the
+// class whatever its depth; only explicit maps are tied to one depth.
 void tune_apply(const NestPlan& p, const TuneChoice& c, hp_level_map* m) {
   if (c.n_map > 0) {
-    for (int l = 0; l < p.depth; ++l) m[l] = c.map[l];
+    if (c.n_map == p.depth) {
+      for (int l = 0; l < p.depth; ++l) m[l] = c.map[l];
+    } else {
+      auto_map(p, m);
+    }
     return;
   }
   if (c.red_hw == HP_HW_AUTO) {
@@ -124,12 +131,19 @@ void tune_apply(const NestPlan& p, const TuneChoice& c, hp_level_map* m) {
   for (int l = r; l < d; ++l) R *= p.ext[l];
   for (int l = 0; l < d; ++l) m[l] = {HP_HW_GRID, 0, 0};
   if (r == d) return;
-  if (c.split_parts > 0) {
+  const bool mixed = c.inner_hw != HP_HW_AUTO;
+  if (c.split_parts > 0 && !mixed) {
     const int64_t tile = std::max<int64_t>(1, (R + c.split_parts - 1) / c.split_parts);
     for (int l = r; l < d; ++l) m[l] = {HP_HW_GRID, 0, l == r ? tile : 0};
     return;
   }
-  for (int l = r; l < d; ++l) m[l] = {c.red_hw, c.sub, 0};
+  if (c.split_parts > 0) {   // the first reduced level split over grid parts, the inner ones on inner_hw
+    m[r] = {HP_HW_GRID, 0, std::max<int64_t>(1, (p.ext[r] + c.split_parts - 1) / c.split_parts)};
+  } else {
+    m[r] = {c.red_hw, c.sub, 0};
+  }
+  for (int l = r + 1; l < d; ++l)
+    m[l] = mixed ? hp_level_map{c.inner_hw, c.inner_sub, 0} : hp_level_map{c.red_hw, c.sub, 0};
 }
 
 static void auto_map(const NestPlan& p, hp_level_map* m) {
@@ -242,11 +256,20 @@ hp_status plan_rect(int depth, const int64_t* extents, const hp_level_map* map, 
   if (all_auto) {
     TuneChoice tc;
     if (red_level < depth && tune_lookup(tune_key(p), &tc)) {
-      tune_apply(p, tc, p.map);
-      p.tuned = true;
-    } else {
-      auto_map(p, p.map);
+      // the shape class's tuned binding, if it is legal for this nest's own
+      // levels (a class spans several depths); else the planner's map
+      hp_level_map tm[HP_MAX_DEPTH];
+      tune_apply(p, tc, tm);
+      NestPlan tp;
+      std::string twhy;
+      if (plan_rect(depth, extents, tm, op, red_level, prec, body, body_params, &tp, &twhy) == HP_OK) {
+        tp.auto_map = true;
+        tp.tuned = true;
+        *out = tp;
+        return HP_OK;
+      }
     }
+    auto_map(p, p.map);
   }
   else
     for (int l = 0; l < depth; ++l) p.map[l] = map[l];

@@ -48,12 +48,15 @@ std::vector<TuneChoice> candidates(const NestPlan& p, int sms, bool with_auto, b
     t.split_parts = parts;
     c.push_back(t);
   };
-  // an explicit map: outputs on the grid, the first reduced level on `first`,
-  // the inner reduced levels on `inner` (a per-level binding)
-  auto add_map = [&](hp_level_map first, hp_level_map inner) {
+  // a per-level binding: the first reduced level on (hw, sub) (or split over
+  // `parts` grid parts), the inner reduced levels on (ihw, isub)
+  auto add_map = [&](int hw, int sub, int64_t parts, int ihw, int isub) {
     TuneChoice t;
-    t.n_map = d;
-    for (int l = 0; l < d; ++l) t.map[l] = l < r ? hp_level_map{HP_HW_GRID, 0, 0} : l == r ? first : inner;
+    t.red_hw = hw;
+    t.sub = sub;
+    t.split_parts = parts;
+    t.inner_hw = ihw;
+    t.inner_sub = isub;
     c.push_back(t);
   };
   if (!batched && R >= 8192) {
@@ -62,21 +65,21 @@ std::vector<TuneChoice> candidates(const NestPlan& p, int sms, bool with_auto, b
       if (R / C < 2048) continue;
       if (d - r >= 2) {
         for (int W : {4, 8})
-          if (R / (static_cast<int64_t>(C) * W * 32) >= 8) add_map({HP_HW_CLUSTER, C, 0}, {HP_HW_CTA, W, 0});
+          if (R / (static_cast<int64_t>(C) * W * 32) >= 8) add_map(HP_HW_CLUSTER, C, 0, HP_HW_CTA, W);
       } else {
-        add_map({HP_HW_CLUSTER, C, 0}, {HP_HW_CLUSTER, C, 0});
+        add(HP_HW_CLUSTER, C, 0);
       }
     }
   }
   if (d - r >= 2 && R >= 1024) {
     // mixed per-level bindings: the warps of a CTA over the first reduced
     // level, the lanes of each warp over the inner ones
-    for (int W : {4, 8}) add_map({HP_HW_CTA, W, 0}, {HP_HW_WARP, 0, 0});
+    for (int W : {4, 8}) add_map(HP_HW_CTA, W, 0, HP_HW_WARP, 0);
     if (R >= 65536 && O < 8 * sms) {
       // the first reduced level split over grid parts, a CTA over the rest
       const int64_t n0 = p.ext[r];
       const int64_t parts = std::max<int64_t>(2, (2 * static_cast<int64_t>(sms) + O - 1) / std::max<int64_t>(O, 1));
-      if (n0 >= 2 * parts) add_map({HP_HW_GRID, 0, (n0 + parts - 1) / parts}, {HP_HW_CTA, 8, 0});
+      if (n0 >= 2 * parts) add_map(HP_HW_GRID, 0, parts, HP_HW_CTA, 8);
     }
   }
   if (R <= 64) add(HP_HW_SEQ, 0, 0);

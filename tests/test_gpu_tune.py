@@ -78,3 +78,33 @@ def test_tune_under_level_requirements(ext, req, allowed):
     assert not fresh.describe()["tuned"]
     fresh.close()
     n.close()
+
+
+def test_tuned_class_applies_across_depths():
+    # a shape class (log2 outputs, log2 reduced size, ...) spans nests of
+    # different depths: the binding tuned on a 4-level nest (with per-level
+    # and cluster candidates) must give every later automatic nest of the
+    # class a legal plan, or the planner's own map, and correct results
+    import torch
+    rng = np.random.Generator(np.random.PCG64(11))
+    ext_a = [3, 5, 64, 1024]          # 15 outputs x 2^16 reduced, two reduced levels
+    A = rng.standard_normal(int(np.prod(ext_a))).astype(np.float32)
+    dA = torch.from_numpy(A).cuda()
+    out = torch.empty(15, dtype=torch.float32, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    n = hb.Nest(ext_a, 2, "sum", "f32_comp", "load")
+    n.tune([dA.data_ptr()], out.data_ptr(), s, retime=True)
+    torch.cuda.synchronize()
+    assert_close(out.cpu().numpy(), oracle_rect(ext_a, 2, "sum", "f32_comp", "load", A=A), "f32_comp", "sum",
+                 n.error_bound(), what=f"tuned {n.describe()['map']}")
+    n.close()
+    for ext_b, r in (([15, 65536], 1), ([15, 2, 8, 4096], 1), ([5, 3, 65536], 2)):
+        B = rng.standard_normal(int(np.prod(ext_b))).astype(np.float32)
+        dB = torch.from_numpy(B).cuda()
+        nb = hb.Nest(ext_b, r, "sum", "f32_comp", "load")
+        ob = torch.empty(15, dtype=torch.float32, device="cuda")
+        nb.run([dB.data_ptr()], ob.data_ptr(), s)
+        torch.cuda.synchronize()
+        assert_close(ob.cpu().numpy(), oracle_rect(ext_b, r, "sum", "f32_comp", "load", A=B), "f32_comp", "sum",
+                     nb.error_bound(), what=f"{ext_b} {nb.describe()['map']}")
+        nb.close()
