@@ -280,6 +280,10 @@ hp_status hp_nest_run_comp(hp_nest *n, const void *const *in_dev, void *out_dev,
  * End-to-end run with HOST buffers: copies the inputs to device staging
  * buffers owned by the nest, runs, copies the outputs back, and waits for the
  * stream.  in_host / out_host are host pointers (pinned memory is fastest).
+ * When the first (streamed) input is page-locked host memory that the device
+ * maps (cudaHostAlloc / cudaMallocHost, or registered memory) and the option
+ * "host_zero_copy" is 1 (the default), the kernel reads it in place over the
+ * host link instead of after a staging copy; results are the same bits.
  * CSR nests are not supported here (HP_EUNSUPPORTED).
  */
 hp_status hp_nest_run_host(hp_nest *n, const void *const *in_host, void *out_host, void *stream);
@@ -595,6 +599,8 @@ void hp_stencil_destroy(hp_stencil *s);
  *               batched steps; 0: servers launch each request alone.
  *   "tune_log"  0 (default); 1: hp_nest_tune* write every candidate's map,
  *               kernel and time to stderr.
+ *   "host_zero_copy"  1 (default): hp_nest_run_host reads a mapped page-locked
+ *               first input in place; 0: always through a staging copy.
  * HP_EINVAL for an unknown name.
  */
 hp_status hp_set_option(const char *name, int64_t value);

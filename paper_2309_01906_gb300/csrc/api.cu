@@ -166,6 +166,10 @@ hp_status hp_set_option(const char* name, int64_t value) {
     options().tune_log = value;
     return HP_OK;
   }
+  if (n == "host_zero_copy") {
+    options().host_zero_copy = value;
+    return HP_OK;
+  }
   return fail(HP_EINVAL, "unknown option " + n);
 }
 
@@ -182,6 +186,10 @@ hp_status hp_get_option(const char* name, int64_t* value) {
   }
   if (n == "tune_log") {
     *value = options().tune_log;
+    return HP_OK;
+  }
+  if (n == "host_zero_copy") {
+    *value = options().host_zero_copy;
     return HP_OK;
   }
   return fail(HP_EINVAL, "unknown option " + n);
@@ -256,6 +264,20 @@ hp_status hp_nest_run_host(hp_nest* n, const void* const* in_host, void* out_hos
   for (int i = 0; i < p.n_inputs; ++i) {
     if (!in_host || !in_host[i]) return fail(HP_EINVAL, "missing host input " + std::to_string(i));
     const size_t b = static_cast<size_t>(p.in_elems[i]) * p.in_elem_bytes;
+    // The streamed input (every element read once per run) may be read by the
+    // kernel straight from page-locked host memory that the device maps: on a
+    // Grace-Blackwell node the kernel's own loads cross the chip-to-chip link
+    // faster than a copy-engine transfer, and no staging copy precedes the run.
+    // The broadcast operand is re-read by every output, so it is staged.
+    if (i == 0 && options().host_zero_copy) {
+      cudaPointerAttributes at{};
+      if (cudaPointerGetAttributes(&at, in_host[i]) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+          at.devicePointer != nullptr && (p.rp.V != 4 || (reinterpret_cast<uintptr_t>(at.devicePointer) & 15u) == 0)) {
+        dev_in[i] = at.devicePointer;
+        continue;
+      }
+      cudaGetLastError();   // a pointer CUDA does not know is not an error here
+    }
     if (n->stage_in_bytes[i] < b) {
       if (n->stage_in[i]) cudaFree(n->stage_in[i]);
       n->stage_in[i] = nullptr;

@@ -476,24 +476,11 @@ __global__ void __launch_bounds__(kCsrCtaThreads, HP_CSR_MIN_BLOCKS) csr_cta_ker
   int64_t start = 0;
   for (int c = 0; c < 3; ++c) start += counters[c];
   const int64_t count = counters[3];
-  const int64_t G = gridDim.x;
   int buf = 0;
-  // the row id two rows ahead and the offsets one row ahead are loaded before
-  // the current row's fold, so that their dependent loads overlap it
-  int64_t k = blockIdx.x;
-  int32_t row = k < count ? rows[start + k] : 0;
-  int32_t row1 = k + G < count ? rows[start + k + G] : 0;
-  int64_t s0 = k < count ? a.off[row] : 0, e0 = k < count ? a.off[row + 1] : 0;
-  for (; k < count; k += G, buf ^= 1) {
-    const int32_t row2 = k + 2 * G < count ? rows[start + k + 2 * G] : 0;
-    const int64_t s1 = k + G < count ? a.off[row1] : 0;
-    const int64_t e1 = k + G < count ? a.off[row1 + 1] : 0;
-    const typename Op::Acc r = cta_fold<Op, HIST>(a, sh_hist, s0, e0, wsh[buf]);
+  for (int64_t k = blockIdx.x; k < count; k += gridDim.x, buf ^= 1) {
+    const int32_t row = rows[start + k];
+    const typename Op::Acc r = cta_fold<Op, HIST>(a, sh_hist, a.off[row], a.off[row + 1], wsh[buf]);
     if (threadIdx.x == 0) a.y[row] = Op::finish(r);
-    row = row1;
-    row1 = row2;
-    s0 = s1;
-    e0 = e1;
   }
   if constexpr (HIST) {
     if (a.smem_bins) hist_flush(a, sh_hist);
@@ -513,38 +500,15 @@ __global__ void __launch_bounds__(kCsrCtaThreads, HP_CSR_MIN_BLOCKS) csr_split_k
     if (a.smem_bins) hist_init(sh_hist, a.smem_bins);
   }
   const int64_t n_slots = counters[11] < max_chunks ? counters[11] : max_chunks;
-  const int64_t G = gridDim.x;
   int buf = 0;
-  // a chunk's range: [off[row] + c * chunk, min(that + chunk, off[row + 1]))
-  auto range = [&](int32_t row, int32_t c, int64_t& s, int64_t& e) {
-    s = a.off[row] + static_cast<int64_t>(c) * kCsrChunk;
-    const int64_t end = a.off[row + 1];
-    e = (s + kCsrChunk < end) ? s + kCsrChunk : end;
-  };
-  // the slot two chunks ahead and the offsets one chunk ahead are loaded
-  // before the current chunk's fold, so that their dependent loads overlap it
-  int64_t k = blockIdx.x;
-  int32_t row1 = 0, c1 = 0;
-  int64_t s0 = 0, e0 = 0;
-  if (k < n_slots) range(chunk_row[k], chunk_idx[k], s0, e0);
-  if (k + G < n_slots) {
-    row1 = chunk_row[k + G];
-    c1 = chunk_idx[k + G];
-  }
-  for (; k < n_slots; k += G, buf ^= 1) {
-    int32_t row2 = 0, c2 = 0;
-    if (k + 2 * G < n_slots) {
-      row2 = chunk_row[k + 2 * G];
-      c2 = chunk_idx[k + 2 * G];
-    }
-    int64_t s1 = 0, e1 = 0;
-    if (k + G < n_slots) range(row1, c1, s1, e1);
-    const typename Op::Acc r = cta_fold<Op, HIST>(a, sh_hist, s0, e0, wsh[buf]);
+  for (int64_t k = blockIdx.x; k < n_slots; k += gridDim.x, buf ^= 1) {
+    const int32_t row = chunk_row[k];
+    const int64_t c = chunk_idx[k];
+    const int64_t s = a.off[row] + c * kCsrChunk;
+    const int64_t e0 = a.off[row + 1];
+    const int64_t e = (s + kCsrChunk < e0) ? s + kCsrChunk : e0;
+    const typename Op::Acc r = cta_fold<Op, HIST>(a, sh_hist, s, e, wsh[buf]);
     if (threadIdx.x == 0) part[k] = r;
-    row1 = row2;
-    c1 = c2;
-    s0 = s1;
-    e0 = e1;
   }
   if constexpr (HIST) {
     if (a.smem_bins) hist_flush(a, sh_hist);

@@ -179,6 +179,7 @@ struct Options {
   int64_t pipeline = 1;    // allow the cp.async-pipelined block kernel
   int64_t serve_batching = 1;  // servers created now pack admitted requests into batched steps
   int64_t tune_log = 0;    // the tuner writes each candidate's map and time to stderr
+  int64_t host_zero_copy = 1;  // hp_nest_run_host reads a mapped page-locked streamed input in place
 };
 Options& options();
 

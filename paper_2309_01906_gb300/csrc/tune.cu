@@ -71,9 +71,11 @@ std::vector<TuneChoice> candidates(const NestPlan& p, int sms, bool with_auto, b
       }
     }
   }
-  if (d - r >= 2 && R >= 1024) {
+  if (!batched && d - r >= 2 && R >= 1024) {
     // mixed per-level bindings: the warps of a CTA over the first reduced
-    // level, the lanes of each warp over the inner ones
+    // level, the lanes of each warp over the inner ones (single runs only: the
+    // batched executor streams a nest through its ring only when the reduced
+    // levels collapse into one)
     for (int W : {4, 8}) add_map(HP_HW_CTA, W, 0, HP_HW_WARP, 0);
     if (R >= 65536 && O < 8 * sms) {
       // the first reduced level split over grid parts, a CTA over the rest

@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 from paper_2309_01906_gb300 import synth
-from tests.hp_testutil import assert_close, gpu_rect, oracle_rect
+from tests.hp_testutil import assert_close, gpu_rect, oracle_rect, out_dtype
 
 pytestmark = pytest.mark.gpu
 
@@ -255,3 +255,41 @@ def test_compensation_output(ext, r, lm):
     else:
         # one body value per output: out + comp is the exact FP32 x FP32 product
         assert np.all(dw_err == 0)
+
+
+@pytest.mark.parametrize("ext,r,prec,lm", [
+    ([3, 7, 16, 132], 2, "f32_comp", [("grid", 0, 0), ("grid", 0, 0), ("cluster", 4, 0), ("cta", 4, 0)]),  # pipelined cluster
+    ([37, 1029], 1, "f32", ["grid", "warp"]),
+    ([7, 1 << 16], 1, "f32_comp", [("grid", 0, 0), ("grid", 0, 4096)]),
+    ([40, 1028], 1, "i32", ["grid", ("cta", 4, 0)]),
+])
+def test_run_host_matches_device_run(ext, r, prec, lm):
+    # hp_nest_run_host with host buffers: the streamed input read in place from
+    # page-locked memory (zero copy), through a staging copy (option off, and
+    # pageable memory): the same bits as hp_nest_run on device copies
+    import torch
+    from paper_2309_01906_gb300 import binding as hb
+    A, w = _inputs(ext, r, prec, "dot_bcast")
+    O = int(np.prod(ext[:r]))
+    dt = out_dtype(prec)
+    n = hb.Nest(ext, r, "sum", prec, "dot_bcast", level_map=lm)
+    try:
+        s = torch.cuda.current_stream().cuda_stream
+        dA, dw = torch.from_numpy(A).cuda(), torch.from_numpy(w).cuda()
+        want = torch.empty(O, dtype=dt, device="cuda")
+        n.run([dA.data_ptr(), dw.data_ptr()], want.data_ptr(), s)
+        torch.cuda.synchronize()
+        want = want.cpu()
+        hA, hw = torch.from_numpy(A).pin_memory(), torch.from_numpy(w).pin_memory()
+        for zero_copy, pinned in ((1, True), (0, True), (1, False)):
+            hb.hp_set_option("host_zero_copy", zero_copy)
+            try:
+                out = torch.full((O,), 7, dtype=dt).pin_memory() if pinned else torch.full((O,), 7, dtype=dt)
+                a_ptr = hA.data_ptr() if pinned else A.ctypes.data
+                w_ptr = hw.data_ptr() if pinned else w.ctypes.data
+                n.run_host([a_ptr, w_ptr], out.data_ptr(), s)
+            finally:
+                hb.hp_set_option("host_zero_copy", 1)
+            assert torch.equal(out, want), (zero_copy, pinned)
+    finally:
+        n.close()
