@@ -35,9 +35,6 @@ constexpr int kStencilMaxR = 4;
 constexpr int kStencilMaxSteps = 8;
 constexpr int kStencilBox = 256;                 // largest tensor-copy box side (points)
 constexpr size_t kStencilSmem = 226 * 1024;      // dynamic shared memory of one CTA (opt-in maximum less static use)
-#ifndef HP_STENCIL_STEP1_PREFETCH
-#define HP_STENCIL_STEP1_PREFETCH 1              // one step: copy the next tile while computing this one
-#endif
 
 struct StencilPlan {
   int64_t ny = 0, nx = 0;
@@ -79,9 +76,7 @@ hp_status plan_stencil(int64_t ny, int64_t nx, int radius, const float* coeffs, 
   std::memcpy(p.c, coeffs, sizeof(float) * K);
   p.h = radius * steps;
   p.hx = round_up(p.h, 4);
-  // fused steps ping-pong between two buffers; one step reads its tile from
-  // one buffer while the next tile's tensor copy fills the other
-  p.nbuf = (steps > 1 || HP_STENCIL_STEP1_PREFETCH) ? 2 : 1;
+  p.nbuf = steps > 1 ? 2 : 1;
   auto box_smem = [&](int ty, int tx) {
     const int bw = tx + 2 * p.hx, bh = ty + 2 * p.h;
     return static_cast<size_t>(p.nbuf) * round_up(bw * bh, 32) * sizeof(float);
@@ -171,7 +166,6 @@ struct StencilArgs {
   int32_t* err;
   int64_t ny, nx;
   int32_t n_tiles, T, TY, TX, h, hx, boxW, boxH, buf_floats, use_tma;
-  int32_t prefetch;         // one step with two buffers and tensor copies: double-buffered tiles
   float c[(2 * kStencilMaxR + 1) * (2 * kStencilMaxR + 1)];
 };
 
@@ -285,68 +279,6 @@ __device__ __forceinline__ void strip(const float* __restrict__ src, float* __re
     checked_strip<R, S>(src, dst, a, i, j0, n, final, gy, gx);
 }
 
-// issue the tensor copy of tile k (tile plus ghost border) into buf, completion on bar
-__device__ __forceinline__ void stencil_issue_copy(const CUtensorMap& tmap, const StencilArgs& a, int k, float* buf,
-                                                   uint32_t bar) {
-  const int64_t gy0 = static_cast<int64_t>(a.order[2 * k]) * a.TY - a.h;
-  const int64_t gx0 = static_cast<int64_t>(a.order[2 * k + 1]) * a.TX - a.hx;
-  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");   // earlier reads of buf before the copy
-  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar),
-               "r"(static_cast<uint32_t>(a.boxW * a.boxH * 4))
-               : "memory");
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
-          smem_addr(buf)),
-      "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(static_cast<int32_t>(gx0)), "r"(static_cast<int32_t>(gy0)), "r"(bar)
-      : "memory");
-}
-
-// One step, tiles double-buffered: while the CTA computes tile i from one
-// buffer, the tensor copy of its next tile fills the other.  Each buffer has
-// its own mbarrier; a buffer is refilled only after the barrier that ends the
-// step computed from it.  Waits are bounded (1 s): one that runs out flags the
-// error word, waits (bounded) for the other copy in flight and leaves.
-template <int R>
-__device__ __forceinline__ void stencil_step_prefetched(const CUtensorMap& tmap, const StencilArgs& a, float* sbuf,
-                                                        uint32_t bar0, unsigned long long& bar1_word, int& ok_flag) {
-  const int tid = threadIdx.x;
-  const uint32_t bars[2] = {bar0, smem_addr(&bar1_word)};
-  float* bufs[2] = {sbuf, sbuf + a.buf_floats};
-  uint32_t parity[2] = {0u, 0u};
-  int k = blockIdx.x;
-  if (tid == 0 && k < a.n_tiles) stencil_issue_copy(tmap, a, k, bufs[0], bars[0]);
-  for (int i = 0; k < a.n_tiles; k += gridDim.x, ++i) {
-    const int b = i & 1;
-    const int kn = k + gridDim.x;
-    if (tid == 0) {
-      if (kn < a.n_tiles) stencil_issue_copy(tmap, a, kn, bufs[b ^ 1], bars[b ^ 1]);
-      int ok = 1;
-      if (!bar_wait(bars[b], parity[b])) {
-        ok = 0;
-        atomicExch(a.err, 1);
-        bar_wait(bars[b], parity[b]);                                  // this copy, another second
-        if (kn < a.n_tiles) bar_wait(bars[b ^ 1], parity[b ^ 1]);     // and the next one
-      }
-      ok_flag = ok;
-    }
-    parity[b] ^= 1u;
-    __syncthreads();
-    if (!ok_flag) return;   // every thread reads the same flag after the barrier
-    const float* src = bufs[b];
-    const int64_t gy0 = static_cast<int64_t>(a.order[2 * k]) * a.TY - a.h;
-    const int64_t gx0 = static_cast<int64_t>(a.order[2 * k + 1]) * a.TX - a.hx;
-    const int jl = a.h, jh = a.h + a.TY, il = a.hx, ih = a.hx + a.TX;
-    constexpr int S = R <= 1 ? 16 : (R == 2 ? 8 : 4);
-    const int H = jh - jl, W = ih - il, n_rs = (H + S - 1) / S;
-    for (int q = tid; q < W * n_rs; q += kStencilThreads) {
-      const int rs = q / W, c = il + (q - rs * W);
-      const int j0 = jl + rs * S, n = min(S, jh - j0);
-      strip<R, S>(src, bufs[b ^ 1], a, c, j0, n, true, gy0, gx0);   // the last step writes global memory only
-    }
-    __syncthreads();   // every read of bufs[b] is done before its next refill
-  }
-}
-
 // FUSED: more than one step per launch (two buffers: 2 CTAs per SM at most,
 // so registers are spent on instruction-level parallelism); one step: radius
 // <= 1 keeps 4 CTAs per SM resident for memory-level parallelism
@@ -358,25 +290,17 @@ __global__ void __launch_bounds__(kStencilThreads, R >= 4 ? 1 : ((R >= 2 || FUSE
     stencil_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ StencilArgs a) {
   extern __shared__ __align__(128) float sbuf[];
   __shared__ __align__(8) unsigned long long bar_word;
-  __shared__ __align__(8) unsigned long long bar2_word;
   __shared__ int ok_flag;
   const int tid = threadIdx.x;
   const uint32_t bar = smem_addr(&bar_word);
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&bar2_word)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   __syncthreads();
   uint32_t parity = 0;
   float* buf0 = sbuf;
   float* buf1 = sbuf + a.buf_floats;
-  if constexpr (!FUSED) {
-    if (a.prefetch) {
-      stencil_step_prefetched<R>(tmap, a, sbuf, bar, bar2_word, ok_flag);
-      return;
-    }
-  }
   for (int k = blockIdx.x; k < a.n_tiles; k += gridDim.x) {
     const int64_t y0 = static_cast<int64_t>(a.order[2 * k]) * a.TY;
     const int64_t x0 = static_cast<int64_t>(a.order[2 * k + 1]) * a.TX;
@@ -580,7 +504,6 @@ extern "C" hp_status hp_stencil_run(hp_stencil* s, const float* in_dev, float* o
   args.boxW = p.boxW;
   args.boxH = p.boxH;
   args.buf_floats = p.buf_floats;
-  args.prefetch = 0;
   std::memcpy(args.c, p.c, sizeof(args.c));
   CUtensorMap tmap;
   {
@@ -594,7 +517,6 @@ extern "C" hp_status hp_stencil_run(hp_stencil* s, const float* in_dev, float* o
     if (args.use_tma) tmap = s->tmap;
     else std::memset(&tmap, 0, sizeof(tmap));
   }
-  args.prefetch = (args.use_tma && p.T == 1 && p.nbuf == 2) ? 1 : 0;
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   cudaError_t e;
   switch (p.r) {

@@ -35,9 +35,7 @@ def test_ghost_border_and_box(r, T):
     assert h == r * T and hx % 4 == 0 and h <= hx < h + 4
     ty, tx = d["tile"]
     assert d["box"] == [ty + 2 * h, tx + 2 * hx] and max(d["box"]) <= 256
-    # two buffers: fused steps ping-pong between them; one step computes a tile
-    # from one while the next tile's tensor copy fills the other
-    assert d["smem"] <= 226 * 1024 and d["buffers"] == 2
+    assert d["smem"] <= 226 * 1024 and d["buffers"] == (2 if T > 1 else 1)
     assert d["tiles"] == -(-3000 // ty) * -(-2000 // tx)
     assert ty >= min(64, 2 * h)        # no tile much shorter than its ghost border
 
