@@ -8,7 +8,10 @@
 // With several streams, steps overlap on the device and requests that arrive
 // while others run join the next step.  Completion is observed by querying the
 // step's event; the scheduler then frees the slots, memory and scratch and
-// admits more.  No device code waits on anything.
+// admits more.  While steps are in flight the scheduler polls their events
+// without sleeping (it owns one host core); with nothing in flight it waits
+// on a condition variable that hp_serve_submit signals.  No device code waits
+// on anything.
 //
 // Every request runs its nest's own plan with the single-run reduction tree
 // (the batched kernels are bit-identical to hp_nest_run), so a result does not
@@ -130,6 +133,7 @@ struct hp_server {
   int device = 0, sms = 0;
   std::mutex mu;
   std::condition_variable cv_done;
+  std::condition_variable cv_work;   // wakes an idle scheduler when a request arrives
   std::deque<uint64_t> queue;
   std::deque<hp::Request> reqs;      // ticket t is reqs[t - 1]; elements never move
   size_t bytes_in_flight = 0;
@@ -353,7 +357,19 @@ void scheduler(hp_server* s) {
       }
       progress = true;
     }
-    if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(5));
+    if (!progress) {
+      // work on the GPU: query its events again at once (the scheduler owns a
+      // host core); nothing in flight: sleep until a request arrives
+      bool busy = false;
+      for (const Step& st : s->steps) busy = busy || st.busy;
+      if (busy) {
+        std::this_thread::yield();
+      } else {
+        std::unique_lock<std::mutex> lock(s->mu);
+        s->cv_work.wait_for(lock, std::chrono::milliseconds(1),
+                            [&] { return !s->queue.empty() || s->stop.load(std::memory_order_relaxed); });
+      }
+    }
   }
 }
 
@@ -442,6 +458,7 @@ hp_status submit(hp_server* s, const hp_nest* shape, const void* const* in_dev, 
   s->reqs.push_back(r);
   *ticket = r.ticket;
   s->queue.push_back(*ticket);
+  s->cv_work.notify_one();
   return HP_OK;
 }
 
@@ -516,7 +533,11 @@ hp_status hp_serve_counters(const hp_server* cs, uint64_t* completed, uint64_t* 
 
 void hp_serve_destroy(hp_server* s) {
   if (!s) return;
-  s->stop.store(true);
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->stop.store(true);
+  }
+  s->cv_work.notify_all();
   if (s->th.joinable()) s->th.join();
   for (Step& st : s->steps) {
     if (st.stream) cudaStreamSynchronize(st.stream);
