@@ -37,7 +37,10 @@
 namespace hp {
 
 constexpr int kCsrClasses = 5;
-constexpr int64_t kCsrLimit0 = 4, kCsrLimit1 = 32, kCsrLimit2 = 1024, kCsrLimit3 = 16384;  // class bounds (inclusive)
+#ifndef HP_CSR_LIMIT1
+#define HP_CSR_LIMIT1 32                                  // longest row of an 8-lane team
+#endif
+constexpr int64_t kCsrLimit0 = 4, kCsrLimit1 = HP_CSR_LIMIT1, kCsrLimit2 = 1024, kCsrLimit3 = 16384;  // class bounds (inclusive)
 constexpr int64_t kCsrChunk = 16384;                      // entries per chunk of a long row
 constexpr int kCsrCtaThreads = 256;
 constexpr int kCsrBinThreads = 256;
@@ -119,7 +122,8 @@ std::string describe_csr(const CsrPlan& p) {
   s << "{\"kind\":\"csr\",\"rows\":" << p.n_rows << ",\"nnz\":" << p.nnz << ",\"cols\":" << p.n_cols
     << ",\"op\":" << static_cast<int>(p.op) << ",\"fuse_hist\":" << p.fuse_hist << ",\"bins\":" << p.n_bins
     << ",\"shift\":" << p.hist_shift << ",\"fixed_class\":" << p.fixed_class
-    << ",\"class_limits\":[4,32,1024,16384],\"chunk\":" << kCsrChunk << "}";
+    << ",\"class_limits\":[" << kCsrLimit0 << "," << kCsrLimit1 << "," << kCsrLimit2 << "," << kCsrLimit3
+    << "],\"chunk\":" << kCsrChunk << "}";
   return s.str();
 }
 
