@@ -574,6 +574,7 @@ def csr_measure(args):
     alg = 8 * csr.nnz + 8 * (n_rows + 1) + 4 * n_cols + 4 * n_rows + 8 * n_bins
     peak, kind = measured_peaks()
     lens = np.diff(csr.offsets)
+    limits = n.describe()["class_limits"]
     gather_rate = csr.nnz / (ms_probe * 1e-3)
     parity, cpu = None, None
     if not args.no_cpu_baseline:
@@ -606,9 +607,9 @@ def csr_measure(args):
                             "probe_ms": ms_probe, "sector_bytes": 32 * csr.nnz,
                             "sector_gbs": 32 * csr.nnz / (ms * 1e-3) / 1e9,
                             "probe_sector_gbs": 32 * gather_rate / 1e9},
-        "rows_by_class": [int(np.sum(lens <= 4)), int(np.sum((lens > 4) & (lens <= 32))),
-                          int(np.sum((lens > 32) & (lens <= 1024))), int(np.sum((lens > 1024) & (lens <= 16384))),
-                          int(np.sum(lens > 16384))],
+        "rows_by_class": [int(np.sum((lens > lo) & (lens <= hi))) for lo, hi in
+                          zip([-1] + limits, limits + [1 << 62])],
+        "class_limits": limits,
         "parity": parity, "cpu_baseline": cpu, "setup_s": setup_s,
         "l2": "inputs larger than L2; no flush (x, 16 MiB, stays in L2 by design)"}
     n.close()

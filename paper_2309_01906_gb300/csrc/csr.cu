@@ -6,7 +6,7 @@
 // time; Sec. 3.8: sub-warp partitions for short rows).  Each run bins the rows
 // by length into classes and runs one kernel per class:
 //   class 0  len <= 4      one thread per row            (SEQ)
-//   class 1  len <= 32     a group of 8 lanes per row     (SUBWARP(8))
+//   class 1  len <= 64     a group of 8 lanes per row     (SUBWARP(8))
 //   class 2  len <= 1024   a warp per row                 (WARP)
 //   class 3  len <= 16384  a CTA of 256 threads per row   (CTA)
 //   class 4  longer        chunks of 16384 entries, a CTA per chunk writing
@@ -38,7 +38,7 @@ namespace hp {
 
 constexpr int kCsrClasses = 5;
 #ifndef HP_CSR_LIMIT1
-#define HP_CSR_LIMIT1 32                                  // longest row of an 8-lane team
+#define HP_CSR_LIMIT1 64                                  // longest row of an 8-lane team (32: 6.44 ms, 64: 6.40, 128: 6.42 on the Zipf workload)
 #endif
 constexpr int64_t kCsrLimit0 = 4, kCsrLimit1 = HP_CSR_LIMIT1, kCsrLimit2 = 1024, kCsrLimit3 = 16384;  // class bounds (inclusive)
 constexpr int64_t kCsrChunk = 16384;                      // entries per chunk of a long row
