@@ -397,9 +397,9 @@ hp_status hp_probe_gather(const float *x_dev, int64_t n_x, int64_t n_gathers, ui
  * for bit.  With hp_set_option("serve_batching", 0) servers created afterwards
  * launch every admitted request alone with the single-nest kernels (the plain
  * per-request baseline).  Completion is observed on the host by event queries:
- * while steps are in flight the scheduler thread polls them without sleeping
- * (it occupies one host core), and with nothing in flight it sleeps until a
- * submission wakes it.  No device code waits. */
+ * while steps are in flight, and for 2 ms after its last activity, the
+ * scheduler thread polls without sleeping (it occupies one host core); idle
+ * longer, it sleeps until a submission wakes it.  No device code waits. */
 
 /* mem_budget_bytes: admission budget (inputs + outputs + scratch of admitted
  * requests); max_slots: requests resident at once; n_streams (1..64): CUDA

@@ -8,10 +8,10 @@
 // With several streams, steps overlap on the device and requests that arrive
 // while others run join the next step.  Completion is observed by querying the
 // step's event; the scheduler then frees the slots, memory and scratch and
-// admits more.  While steps are in flight the scheduler polls their events
-// without sleeping (it owns one host core); with nothing in flight it waits
-// on a condition variable that hp_serve_submit signals.  No device code waits
-// on anything.
+// admits more.  While steps are in flight, and for 2 ms after the last
+// activity, the scheduler polls without sleeping (it owns one host core);
+// idle longer, it waits on a condition variable that hp_serve_submit signals.
+// No device code waits on anything.
 //
 // Every request runs its nest's own plan with the single-run reduction tree
 // (the batched kernels are bit-identical to hp_nest_run), so a result does not
@@ -101,7 +101,7 @@ struct Request {
   hp_nest* nest;
   const void* in[2];
   void* out;
- double t_submit;        // arrival: scheduled (hp_serve_submit_at) or the submit call
+  double t_submit;       // arrival: scheduled (hp_serve_submit_at) or the submit call
   size_t bytes;          // inputs + outputs + scratch counted against the budget
   size_t part_bytes, ticket_bytes;
   size_t part_off, ticket_off;
@@ -301,8 +301,12 @@ void finish_step(hp_server* s, Step& st, bool ok) {
   s->cv_done.notify_all();
 }
 
+// how long an idle scheduler keeps polling before it sleeps on the condition variable
+constexpr double kServeSpinUs = 2000.0;
+
 void scheduler(hp_server* s) {
   cudaSetDevice(s->device);
+  double last_active = now_us();
   while (!s->stop.load(std::memory_order_relaxed)) {
     bool progress = false;
     for (Step& st : s->steps) {
@@ -357,12 +361,14 @@ void scheduler(hp_server* s) {
       }
       progress = true;
     }
+    if (progress) last_active = now_us();
     if (!progress) {
-      // work on the GPU: query its events again at once (the scheduler owns a
-      // host core); nothing in flight: sleep until a request arrives
+      // work on the GPU, or activity in the last kServeSpinUs: query again at
+      // once (the scheduler owns a host core); idle longer: sleep until a
+      // request arrives (a wake-up costs tens of microseconds)
       bool busy = false;
       for (const Step& st : s->steps) busy = busy || st.busy;
-      if (busy) {
+      if (busy || now_us() - last_active < kServeSpinUs) {
         std::this_thread::yield();
       } else {
         std::unique_lock<std::mutex> lock(s->mu);
