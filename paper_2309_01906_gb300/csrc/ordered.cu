@@ -193,7 +193,6 @@ __device__ __forceinline__ void ld8(const float* p, float* r) {
 // output whose first iteration is `base`, in order.
 
 struct AffineOp {
-  static constexpr int kMinBlocks1024 = 1;   // launch bound of the block kernel (1024-thread blocks per SM)
   using S = float2;   // (A, B)
   static constexpr int kOut = 2;
   template <int V>
@@ -268,7 +267,6 @@ __device__ __forceinline__ AffineOp::S AffineOp::fold(const OrdArgs& g, int64_t 
 }
 
 struct Mat2Op {
-  static constexpr int kMinBlocks1024 = 1;
   using S = float4;   // (m00, m01, m10, m11)
   static constexpr int kOut = 4;
   template <int V>
@@ -327,11 +325,7 @@ struct Mat2Op {
   }
 };
 
-#ifndef HP_ORD_LAST_MINB
-#define HP_ORD_LAST_MINB 1
-#endif
 struct LastOp {
-  static constexpr int kMinBlocks1024 = HP_ORD_LAST_MINB;
   using S = float;    // the last value that is not NaN so far (NaN: none)
   static constexpr int kOut = 1;
   template <int V>
@@ -424,7 +418,7 @@ __global__ void __launch_bounds__(kOrdThreads) ordered_warp_kernel(OrdArgs g) {
 }
 
 template <class Op, int V>
-__global__ void __launch_bounds__(1024, Op::kMinBlocks1024) ordered_block_kernel(OrdArgs g) {   // W <= 32 warps per team
+__global__ void __launch_bounds__(1024) ordered_block_kernel(OrdArgs g) {   // W <= 32 warps per team
   __shared__ typename Op::S wp[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t items = g.O * g.G;
