@@ -227,46 +227,6 @@ __device__ __forceinline__ void fast_strip(const float* __restrict__ src, float*
   }
 }
 
-// Two adjacent columns i and i + 1, N rows from j0, inside the array: their
-// N + 2R rows of 2R + 2 input columns are loaded once (a column pair shares
-// 2R of its 2R + 2 input columns, so it takes (2R + 2) / (2 (2R + 1)) of the
-// shared-memory loads of two single strips).  Each point is the same FMA chain
-// in the same order as fast_strip's, so the results are the same bits.
-template <int R, int N>
-__device__ __forceinline__ void fast_strip2(const float* __restrict__ src, float* __restrict__ dst,
-                                            const StencilArgs& a, int i, int j0, bool final, int64_t gy, int64_t gx) {
-  constexpr int D = 2 * R + 1, C = D + 1;
-  const int P = a.boxW;
-  const float* sp = src + (j0 - R) * P + (i - R);
-  float v[N + 2 * R][C];
-#pragma unroll
-  for (int y = 0; y < N + 2 * R; ++y)
-#pragma unroll
-    for (int dx = 0; dx < C; ++dx) v[y][dx] = sp[y * P + dx];
-  float* dp = dst + j0 * P + i;
-  float* gp = a.out + (gy * a.nx + gx);
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-    float acc0 = 0.0f, acc1 = 0.0f;
-#pragma unroll
-    for (int dy = 0; dy < D; ++dy)
-#pragma unroll
-      for (int dx = 0; dx < D; ++dx) {
-        acc0 = __fmaf_rn(a.c[dy * D + dx], v[k + dy][dx], acc0);
-        acc1 = __fmaf_rn(a.c[dy * D + dx], v[k + dy][dx + 1], acc1);
-      }
-    if (final) {
-      gp[0] = acc0;
-      gp[1] = acc1;
-      gp += a.nx;
-    } else {
-      dp[0] = acc0;
-      dp[1] = acc1;
-      dp += P;
-    }
-  }
-}
-
 // rows [j0, j0 + n) of buffer column i, any position: a sliding window of
 // 2R+1 rows x 2R+1 columns in registers and per-point array checks (points
 // outside the array: not stored in the last step, 0 in the others)
@@ -322,9 +282,6 @@ __device__ __forceinline__ void strip(const float* __restrict__ src, float* __re
 // FUSED: more than one step per launch (two buffers: 2 CTAs per SM at most,
 // so registers are spent on instruction-level parallelism); one step: radius
 // <= 1 keeps 4 CTAs per SM resident for memory-level parallelism
-#ifndef HP_STENCIL_PAIRS
-#define HP_STENCIL_PAIRS 1          // fused steps (radius <= 2): a thread takes a pair of adjacent columns
-#endif
 #ifndef HP_STENCIL_STEP1_BLOCKS
 #define HP_STENCIL_STEP1_BLOCKS 3   // resident CTAs per SM the one-step kernels' registers are sized for (measured best)
 #endif
@@ -394,28 +351,10 @@ __global__ void __launch_bounds__(kStencilThreads, R >= 4 ? 1 : ((R >= 2 || FUSE
       constexpr int S = R <= 1 ? 16 : (R == 2 ? 8 : 4);   // S + 2R rows of 2R+1 registers
       const int H = jh - jl, W = ih - il, n_rs = (H + S - 1) / S;
       const bool final = s == a.T;
-      if constexpr (FUSED && R <= 2 && HP_STENCIL_PAIRS) {
-        // fused steps are bound by shared-memory loads: a thread takes two
-        // adjacent columns of a strip, which share most of their inputs
-        constexpr int S2 = R <= 1 ? 8 : 4;
-        const int W2 = (W + 1) / 2, n_rs2 = (H + S2 - 1) / S2;
-        for (int q = tid; q < W2 * n_rs2; q += kStencilThreads) {
-          const int rs = q / W2, i = il + 2 * (q - rs * W2);
-          const int j0 = jl + rs * S2, n = min(S2, jh - j0);
-          const int64_t gx = gx0 + i, gy = gy0 + j0;
-          if (i + 1 < ih && n == S2 && gx >= 0 && gx + 1 < a.nx && gy >= 0 && gy + S2 <= a.ny) {
-            fast_strip2<R, S2>(src, dst, a, i, j0, final, gy, gx);
-          } else {
-            strip<R, S2>(src, dst, a, i, j0, n, final, gy0, gx0);
-            if (i + 1 < ih) strip<R, S2>(src, dst, a, i + 1, j0, n, final, gy0, gx0);
-          }
-        }
-      } else {
-        for (int q = tid; q < W * n_rs; q += kStencilThreads) {
-          const int rs = q / W, i = il + (q - rs * W);
-          const int j0 = jl + rs * S, n = min(S, jh - j0);
-          strip<R, S>(src, dst, a, i, j0, n, final, gy0, gx0);
-        }
+      for (int q = tid; q < W * n_rs; q += kStencilThreads) {
+        const int rs = q / W, i = il + (q - rs * W);
+        const int j0 = jl + rs * S, n = min(S, jh - j0);
+        strip<R, S>(src, dst, a, i, j0, n, final, gy0, gx0);
       }
       __syncthreads();
     }
