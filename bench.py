@@ -162,13 +162,15 @@ def write_parity_table(path, idx, got, ref):
     with open(path, "w") as f:
         f.write("output,got,ref_fp64,sum_abs,cond,abs_err,rel_err,norm_err,clause\n")
         for k in range(g.size):
-            e = abs(g[k] - r[k])
-            fl = 2.0 ** -20 * ref.abs_sum[k]
-            clause = "relative" if abs(r[k]) >= fl else "normalized"
-            sc = max(abs(r[k]), fl)
-            f.write(f"{int(idx[k])},{g[k]!r},{r[k]!r},{ref.abs_sum[k]!r},"
-                    f"{(ref.abs_sum[k] / abs(r[k])) if r[k] else float('inf')!r},{e!r},"
-                    f"{(e / abs(r[k])) if r[k] else float('inf')!r},{(e / sc) if sc else 0.0!r},{clause}\n")
+            gk, rk, ak = float(g[k]), float(r[k]), float(ref.abs_sum[k])
+            e = abs(gk - rk)
+            fl = 2.0 ** -20 * ak
+            clause = "relative" if abs(rk) >= fl else "normalized"
+            sc = max(abs(rk), fl)
+            cond = ak / abs(rk) if rk else float("inf")
+            rel = e / abs(rk) if rk else float("inf")
+            norm = e / sc if sc else 0.0
+            f.write(f"{int(idx[k])},{gk!r},{rk!r},{ak!r},{cond!r},{e!r},{rel!r},{norm!r},{clause}\n")
 
 
 def dist_env():
