@@ -121,7 +121,8 @@ def fp_parity(got, ref, prec, bound, tol):
     rel_clause = np.abs(r) >= floor
     scale = np.maximum(np.abs(r), floor)
     safe = np.where(scale > 0, scale, 1.0)
-    norm = np.where(scale > 0, err / safe, np.where(err > 0, np.inf, 0.0))
+    # a nonzero result where every term is zero has no scale: its error counts as 1e300
+    norm = np.where(scale > 0, err / safe, np.where(err > 0, 1e300, 0.0))
     nz = r != 0
     rel = err[nz] / np.abs(r[nz])
     cond = np.where(nz, ab / np.where(nz, np.abs(r), 1.0), np.inf)
