@@ -136,7 +136,7 @@ def fp_parity(got, ref, prec, bound, tol):
         "p50_norm_err": float(np.median(norm)) if norm.size else 0.0,
         "p99_norm_err": float(np.quantile(norm, 0.99)) if norm.size else 0.0,
         "worst": {"index": worst, "got": float(g[worst]), "ref": float(r[worst]), "sum_abs": float(ab[worst]),
-                  "cond": float(cond[worst])} if norm.size else None,
+                  "cond": float(cond[worst]) if np.isfinite(cond[worst]) else None} if norm.size else None,
         "max_plain_rel_err": float(rel.max()) if rel.size else 0.0,
         "max_cond": float(cond[np.isfinite(cond)].max()) if np.isfinite(cond).any() else None,
         "median_cond": float(np.median(cond)) if cond.size else None,
