@@ -40,7 +40,10 @@ constexpr int kCsrClasses = 5;
 #ifndef HP_CSR_LIMIT1
 #define HP_CSR_LIMIT1 64                                  // longest row of an 8-lane team (32: 6.44 ms, 64: 6.40, 128: 6.42 on the Zipf workload)
 #endif
-constexpr int64_t kCsrLimit0 = 4, kCsrLimit1 = HP_CSR_LIMIT1, kCsrLimit2 = 1024, kCsrLimit3 = 16384;  // class bounds (inclusive)
+#ifndef HP_CSR_LIMIT2
+#define HP_CSR_LIMIT2 1024                                // longest row of a warp team
+#endif
+constexpr int64_t kCsrLimit0 = 4, kCsrLimit1 = HP_CSR_LIMIT1, kCsrLimit2 = HP_CSR_LIMIT2, kCsrLimit3 = 16384;  // class bounds (inclusive)
 constexpr int64_t kCsrChunk = 16384;                      // entries per chunk of a long row
 constexpr int kCsrCtaThreads = 256;
 constexpr int kCsrBinThreads = 256;
