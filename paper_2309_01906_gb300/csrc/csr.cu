@@ -7,7 +7,7 @@
 // by length into classes and runs one kernel per class:
 //   class 0  len <= 4      one thread per row            (SEQ)
 //   class 1  len <= 64     a group of 8 lanes per row     (SUBWARP(8))
-//   class 2  len <= 1024   a warp per row                 (WARP)
+//   class 2  len <= 2048   a warp per row                 (WARP)
 //   class 3  len <= 16384  a CTA of 256 threads per row   (CTA)
 //   class 4  longer        chunks of 16384 entries, a CTA per chunk writing
 //                          its partial to the chunk's slot; a second kernel
@@ -41,7 +41,7 @@ constexpr int kCsrClasses = 5;
 #define HP_CSR_LIMIT1 64                                  // longest row of an 8-lane team (32: 6.44 ms, 64: 6.40, 128: 6.42 on the Zipf workload)
 #endif
 #ifndef HP_CSR_LIMIT2
-#define HP_CSR_LIMIT2 1024                                // longest row of a warp team
+#define HP_CSR_LIMIT2 2048                                // longest row of a warp team (1024: 6.42 ms, 2048: 6.37, 4096: 6.37)
 #endif
 constexpr int64_t kCsrLimit0 = 4, kCsrLimit1 = HP_CSR_LIMIT1, kCsrLimit2 = HP_CSR_LIMIT2, kCsrLimit3 = 16384;  // class bounds (inclusive)
 constexpr int64_t kCsrChunk = 16384;                      // entries per chunk of a long row
