@@ -43,9 +43,20 @@ constexpr int kCsrClasses = 5;
 #ifndef HP_CSR_LIMIT2
 #define HP_CSR_LIMIT2 2048                                // longest row of a warp team (1024: 6.42 ms, 2048: 6.37, 4096: 6.37)
 #endif
-constexpr int64_t kCsrLimit0 = 4, kCsrLimit1 = HP_CSR_LIMIT1, kCsrLimit2 = HP_CSR_LIMIT2, kCsrLimit3 = 16384;  // class bounds (inclusive)
-constexpr int64_t kCsrChunk = 16384;                      // entries per chunk of a long row
-constexpr int kCsrCtaThreads = 256;
+#ifndef HP_CSR_LIMIT3
+#define HP_CSR_LIMIT3 16384                               // longest row of a CTA team
+#endif
+#ifndef HP_CSR_CHUNK
+#define HP_CSR_CHUNK 16384                                // entries per chunk of a longer row
+#endif
+constexpr int64_t kCsrLimit0 = 4, kCsrLimit1 = HP_CSR_LIMIT1, kCsrLimit2 = HP_CSR_LIMIT2, kCsrLimit3 = HP_CSR_LIMIT3;  // class bounds (inclusive)
+constexpr int64_t kCsrChunk = HP_CSR_CHUNK;
+static_assert(kCsrLimit3 >= kCsrChunk, "split rows must be longer than one chunk (bounds the chunk slots)");
+constexpr int kCsrCtaThreads = 256;                       // the chunk kernel's CTA
+#ifndef HP_CSR_ROW_CTA_THREADS
+#define HP_CSR_ROW_CTA_THREADS 256                         // the CTA-per-row kernel's CTA
+#endif
+constexpr int kCsrRowCtaThreads = HP_CSR_ROW_CTA_THREADS;
 constexpr int kCsrBinThreads = 256;
 constexpr int kCsrHistSmemMax = 12288;                   // bins counted in shared memory
 #ifndef HP_CSR_GROUPS
@@ -65,6 +76,7 @@ struct CsrState {
   int64_t max_chunks = 0;
   int grid_rows = 0;             // persistent grid sizes
   int grid_cta = 0;
+  int grid_row_cta = 0;
 };
 
 // ---------------------------------------------------------------- planning
@@ -473,10 +485,11 @@ __device__ __forceinline__ typename Op::Acc cta_fold(const CsrArgs& a, int* sh, 
 
 // class 3: a CTA per row
 template <class Op, bool HIST>
-__global__ void __launch_bounds__(kCsrCtaThreads, HP_CSR_MIN_BLOCKS) csr_cta_kernel(CsrArgs a, const int32_t* __restrict__ rows,
+__global__ void __launch_bounds__(kCsrRowCtaThreads, HP_CSR_MIN_BLOCKS * kCsrCtaThreads / kCsrRowCtaThreads)
+    csr_cta_kernel(CsrArgs a, const int32_t* __restrict__ rows,
                                                                  const int64_t* counters) {
   extern __shared__ int sh_hist[];
-  __shared__ typename Op::Acc wsh[2][kCsrCtaThreads / 32];
+  __shared__ typename Op::Acc wsh[2][kCsrRowCtaThreads / 32];
   if constexpr (HIST) {
     if (a.smem_bins) hist_init(sh_hist, a.smem_bins);
   }
@@ -607,7 +620,8 @@ hp_status launch_classes(hp_nest* n, const CsrArgs& a, cudaStream_t st) {
   if (fixed < 0 || fixed == 0) csr_rows_kernel<Op, 1, HIST><<<cs.grid_rows, 256, dyn, st>>>(a, cs.rows, cs.counters, 0);
   if (fixed < 0 || fixed == 1) csr_rows_kernel<Op, 8, HIST><<<cs.grid_rows, 256, dyn, st>>>(a, cs.rows, cs.counters, 1);
   if (fixed < 0 || fixed == 2) csr_rows_kernel<Op, 32, HIST><<<cs.grid_rows, 256, dyn, st>>>(a, cs.rows, cs.counters, 2);
-  if (fixed < 0 || fixed == 3) csr_cta_kernel<Op, HIST><<<cs.grid_cta, kCsrCtaThreads, dyn, st>>>(a, cs.rows, cs.counters);
+  if (fixed < 0 || fixed == 3)
+    csr_cta_kernel<Op, HIST><<<cs.grid_row_cta, kCsrRowCtaThreads, dyn, st>>>(a, cs.rows, cs.counters);
   if (fixed < 0 || fixed == 4) {
     csr_split_kernel<Op, HIST><<<cs.grid_cta, kCsrCtaThreads, dyn, st>>>(
         a, cs.counters, cs.chunk_row, cs.chunk_idx, static_cast<typename Op::Acc*>(cs.part), cs.max_chunks);
@@ -664,6 +678,10 @@ hp_status csr_prepare(hp_nest* n) {
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, csr_split_kernel<OpF32Comp, true>, kCsrCtaThreads,
                                                 smem_bins_for(p.n_bins) * sizeof(int));
   cs->grid_cta = std::max(1, per_sm) * n->sms;
+  per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, csr_cta_kernel<OpF32Comp, true>, kCsrRowCtaThreads,
+                                                smem_bins_for(p.n_bins) * sizeof(int));
+  cs->grid_row_cta = std::max(1, per_sm) * n->sms;
   return HP_OK;
 }
 
