@@ -134,7 +134,9 @@ typedef enum hp_red_op {
  *   HP_F32       FP32 inputs, plain FP32 accumulation (deterministic tree).
  *   HP_F32_COMP  FP32 inputs, compensated FP32 accumulation at every level
  *                (error-free product and sum transformations; Ogita-Rump-
- *                Oishi Dot2), FP64 only in the final grid-level combine.
+ *                Oishi Dot2); grid parts are combined as double-float
+ *                numbers (no FP64 on the GPU: a dependent FP64 operation
+ *                costs about 14 FP32 ones on this GPU).
  *   HP_I32       int32 inputs, int32 accumulation: sums are exact modulo 2^32.
  *   HP_I64       int32 inputs widened to int64, int64 accumulation.
  * Outputs: float for the FP precisions, int32_t / int64_t for the integer ones.
@@ -266,9 +268,9 @@ hp_status hp_nest_run(hp_nest *n, const void *const *in_dev, void *out_dev, void
  * that also writes, for each output, the FP32 compensation of its final
  * rounding: comp_dev[o] is the exact error of out_dev[o] against the
  * two-word sum s + c the reduction tree reached (Sec. 2's recursive
- * reduction, carried in Ogita-Rump-Oishi double-word form), or, when the
- * plan combines grid parts in FP64, the FP64 sum minus out_dev[o] rounded
- * once.  out + comp then carries the result to about 2^-48 relative; |comp|
+ * reduction, carried in Ogita-Rump-Oishi double-word form), also when the
+ * plan combines grid parts (their double-float sum).  out + comp then carries
+ * the result to about 2^-48 relative; |comp|
  * is what the FP32 output gave away, for a caller's own error report.
  *   comp_dev  device pointer, one float per output (same layout as out_dev).
  * out_dev holds the same bits as hp_nest_run's.  HP_EUNSUPPORTED for other
@@ -399,7 +401,25 @@ hp_status hp_probe_gather(const float *x_dev, int64_t n_x, int64_t n_gathers, ui
  * per-request baseline).  Completion is observed on the host by event queries:
  * while steps are in flight, and for 2 ms after its last activity, the
  * scheduler thread polls without sleeping (it occupies one host core); idle
- * longer, it sleeps until a submission wakes it.  No device code waits. */
+ * longer, it sleeps until a submission wakes it.
+ *
+ * With hp_set_option("serve_batching", 2) servers created afterwards keep the
+ * batched persistent kernel resident instead: while the server has work, one
+ * instance of it runs with (resident CTAs per SM - 1) CTAs on every SM (room
+ * for one more CTA of other kernels stays free), and its producer warps take
+ * the tiles of newly admitted requests from a ring in mapped page-locked host
+ * memory that the scheduler fills; a request then reaches the GPU without a
+ * kernel launch, and the CTA that finishes its last tile writes its
+ * completion to a mapped host word that the scheduler polls.  Results are
+ * bit-identical to hp_nest_run as in the batched mode.  An instance takes new
+ * tiles for 100 ms of host time, then the scheduler stops it and starts the
+ * next (they overlap while the old one drains); 2 ms after the server's last
+ * activity it stops the instance and starts a new one on the next admission.
+ * Device waits for tiles are bounded (2 s per wait; the instance then leaves
+ * with an error status, which fails the server's live requests).  A resident
+ * server runs one arithmetic, set by its first request (FP32 sum, compensated
+ * sum, max, min or int32 sum, max, min); other requests get HP_EUNSUPPORTED.
+ * Other kernels on the GPU share it with the instance while it runs. */
 
 /* mem_budget_bytes: admission budget (inputs + outputs + scratch of admitted
  * requests); max_slots: requests resident at once; n_streams (1..64): CUDA
@@ -407,7 +427,10 @@ hp_status hp_probe_gather(const float *x_dev, int64_t n_x, int64_t n_gathers, ui
 hp_status hp_serve_create(size_t mem_budget_bytes, int max_slots, int n_streams, hp_server **out);
 
 /* Submit one request: a nest (shape and plan), its device inputs and output.
- * Returns a ticket.  The server prepares the nest's device state and its
+ * Returns a ticket.  The inputs and the output must be ready when the call is
+ * made: the server orders its work after nothing on the caller's streams, so
+ * writes to them still pending there (a fill, a copy) must be synchronized
+ * first.  The server prepares the nest's device state and its
  * launch configuration on first use, from the scheduler thread, so from
  * submission until every ticket on it is polled done the caller must not run,
  * tune or destroy that nest (hp_nest_run*, hp_nest_tune*, hp_nest_destroy):

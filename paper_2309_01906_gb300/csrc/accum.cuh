@@ -373,4 +373,76 @@ __device__ __forceinline__ void fold_vals_dot(typename Op::Acc (&acc)[V], const 
   }
 }
 
+// ---------------------------------------------------------------- grid parts
+// L2 loads of partials (other SMs of the same launch may have written them)
+__device__ __forceinline__ f2 ld_part(const f2* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return f2{v.x, v.y};
+}
+__device__ __forceinline__ float ld_part(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ uint32_t ld_part(const uint32_t* p) { return __ldcg(p); }
+__device__ __forceinline__ int32_t ld_part(const int32_t* p) { return __ldcg(p); }
+__device__ __forceinline__ unsigned long long ld_part(const unsigned long long* p) { return __ldcg(p); }
+__device__ __forceinline__ long long ld_part(const long long* p) { return __ldcg(p); }
+
+// The final combine of one output's G partials (the second pass of Sec. 2's
+// recursive reduction when a reduced level is split over the grid), shared by
+// every executor so that their results agree bit for bit.  Parts are folded
+// in part order.  Compensated partials (s_g, c_g) are added as double-float
+// numbers: TwoSum carries s_g into the running sum exactly, and its error and
+// c_g go to a second FP32 word (the cascaded summation of Ogita, Rump and
+// Oishi, "Accurate sum and dot product", 2005); the result is the rounded sum
+// of the two words and rem (may be null) its exact rounding error.  Its error
+// is at most gamma_2G (gamma_G + 2 gamma_k) sum|t| beyond the parts' own (k
+// the parts' chain length), far below the FP32 result's rounding.  FP64 is
+// not used: a dependent FP64 operation costs about 63 SM cycles on this GPU
+// (FP32: 4.5), and a chain of 2G of them took about 40 us for G = 304.
+// Loads are issued 8 parts at a time.
+template <class Op>
+__device__ __forceinline__ typename Op::Out combine_parts(const typename Op::Acc* pp, int32_t G, float* rem) {
+  using Acc = typename Op::Acc;
+  constexpr int K = 8;
+  if constexpr (std::is_same_v<Acc, f2>) {
+    float S = 0.0f, C = 0.0f;
+    int32_t g = 0;
+    for (; g + K <= G; g += K) {
+      f2 v[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[k] = ld_part(pp + g + k);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        float s2, e;
+        two_sum(S, v[k].s, s2, e);
+        S = s2;
+        C = __fadd_rn(C, e);
+        C = __fadd_rn(C, v[k].c);
+      }
+    }
+    for (; g < G; ++g) {
+      const f2 v = ld_part(pp + g);
+      float s2, e;
+      two_sum(S, v.s, s2, e);
+      S = s2;
+      C = __fadd_rn(C, e);
+      C = __fadd_rn(C, v.c);
+    }
+    float r, e;
+    two_sum(S, C, r, e);
+    if (rem) *rem = e;
+    return r;
+  } else {
+    Acc a = ld_part(pp);
+    int32_t g = 1;
+    for (; g + K <= G; g += K) {
+      Acc v[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[k] = ld_part(pp + g + k);
+#pragma unroll
+      for (int k = 0; k < K; ++k) a = Op::combine(a, v[k]);
+    }
+    for (; g < G; ++g) a = Op::combine(a, ld_part(pp + g));
+    return Op::finish(a);
+  }
+}
+
 }  // namespace hp

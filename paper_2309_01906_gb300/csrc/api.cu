@@ -159,6 +159,7 @@ hp_status hp_set_option(const char* name, int64_t value) {
     return HP_OK;
   }
   if (n == "serve_batching") {
+    if (value < 0 || value > 2) return fail(HP_EINVAL, "serve_batching is 0 (plain), 1 (batched) or 2 (resident)");
     options().serve_batching = value;
     return HP_OK;
   }

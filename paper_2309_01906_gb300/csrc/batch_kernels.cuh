@@ -5,9 +5,9 @@
 // work items of one nest; it runs with that nest's own plan and with exactly
 // the per-thread fold order and team tree of rect_block_kernel /
 // rect_lanes_kernel, so every nest's outputs equal those of hp_nest_run on it,
-// bit for bit.  Nests split over grid parts fold their parts in part order
-// once the last part of an output has arrived (a per-output ticket counter;
-// nobody waits on it).
+// bit for bit.  Nests split over grid parts fold their parts with
+// rect_combine_kernel's combine (combine_parts) once the last part of an
+// output has arrived (a per-output ticket counter; nobody waits on it).
 //
 // The CTA is warp-specialised.  One producer warp takes the tiles, copies each
 // tile's nest descriptor into a small tile queue in shared memory and, when
@@ -82,6 +82,8 @@ struct BatchQueued {
   uint64_t gA;         // address of the nest's input A
   int32_t nst;         // stages of the stream (0: the tile folds from global memory)
   int32_t end;         // 1: no more tiles
+  int32_t req_tiles;   // resident executor: tiles of the tile's request
+  uint32_t req_seq;    // resident executor: the request's sequence number in its slot
 };
 
 // Can a nest's tiles stream through the ring?  One reduced virtual level of
@@ -121,6 +123,14 @@ struct EmitTo {
   int32_t G;
 };
 
+// the last part of an output to arrive combines them all (the combine of
+// rect_combine_kernel, so results equal hp_nest_run's); out of line, so that
+// its registers do not weigh on the streaming loops that call batch_emit
+template <class Op>
+__device__ __forceinline__ void batch_combine(const typename Op::Acc* pp, int32_t G, typename Op::Out* out) {
+  *out = combine_parts<Op>(pp, G, nullptr);
+}
+
 template <class Op>
 __device__ __forceinline__ void batch_emit(const EmitTo& to, int64_t item, typename Op::Acc a) {
   using Acc = typename Op::Acc;
@@ -134,22 +144,7 @@ __device__ __forceinline__ void batch_emit(const EmitTo& to, int64_t item, typen
   __threadfence();  // publish the partial before taking the ticket
   if (atomicAdd(&to.tickets[o], 1) == to.G - 1) {
     __threadfence();  // all parts of this output are visible
-    const Acc* pp = part + o * to.G;
-    if constexpr (sizeof(Acc) == 8 && Op::kFp) {
-      // compensated partials: the final grid-level combine in FP64, part order
-      const volatile float* pv = reinterpret_cast<const volatile float*>(pp);
-      double s = 0.0;
-      for (int g = 0; g < to.G; ++g) {
-        s += static_cast<double>(pv[2 * g]);
-        s += static_cast<double>(pv[2 * g + 1]);
-      }
-      static_cast<typename Op::Out*>(to.out)[o] = static_cast<float>(s);
-    } else {
-      const volatile Acc* pv = pp;
-      Acc v = pv[0];
-      for (int g = 1; g < to.G; ++g) v = Op::combine(v, pv[g]);
-      static_cast<typename Op::Out*>(to.out)[o] = Op::finish(v);
-    }
+    batch_combine<Op>(part + o * to.G, to.G, static_cast<typename Op::Out*>(to.out) + o);
     to.tickets[o] = 0;  // ready for the next run
   }
 }
@@ -197,18 +192,20 @@ __device__ __forceinline__ void st_abort(uint32_t at) {
 // the slow part of a wait: poll until the phase of parity `parity` completes;
 // false when the CTA's abort flag (shared address abort_at, 0 = none) is set
 // or the wait ran out of time
-static __device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, uint32_t abort_at) {
+static __device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, uint32_t abort_at,
+                                                   unsigned long long limit_ns) {
   const unsigned long long t0 = global_ns();
   for (uint32_t i = 1;; ++i) {
     if (mbar_test(bar, parity)) return true;
     if ((i & 31u) == 0) {
       if (abort_at && ld_abort(abort_at)) return false;
-      if (global_ns() - t0 > kBatchWaitNs) return false;
+      if (global_ns() - t0 > limit_ns) return false;
     }
   }
 }
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t abort_at) {
-  return mbar_test(bar, parity) || mbar_wait_slow(bar, parity, abort_at);
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t abort_at,
+                                          unsigned long long limit_ns = kBatchWaitNs) {
+  return mbar_test(bar, parity) || mbar_wait_slow(bar, parity, abort_at, limit_ns);
 }
 // 1-D bulk copy global -> shared, completion counted on `bar` in bytes
 // (both addresses 16-byte aligned, bytes a multiple of 16)
@@ -745,11 +742,41 @@ __device__ __forceinline__ void ring_tile(const BatchQueued& e, uint32_t ring, c
   }
 }
 
+// ---------------------------------------------------------------- tile sources
+// Where the producer warp takes its tiles from.  claim() runs on lane 0 and
+// returns the index of the next tile, or -1 when there is none; tile() and
+// desc() run on the whole warp after it.
+
+// a tile table in device memory, taken through an atomic counter (one launch)
+struct TableSource {
+  static constexpr bool kResident = false;
+  const BatchNest* __restrict__ nests;
+  const BatchTile* __restrict__ tiles;
+  int64_t n_tiles;
+  unsigned long long* counter;
+
+  __device__ __forceinline__ int64_t claim() const {
+    const int64_t k = static_cast<int64_t>(atomicAdd(counter, 1ull));
+    return k < n_tiles ? k : -1;
+  }
+  __device__ __forceinline__ BatchTile tile(int64_t k) const { return tiles[k]; }
+  __device__ __forceinline__ void desc(int lane, const BatchTile& t, BatchQueued& e) const {
+    const int32_t* src = reinterpret_cast<const int32_t*>(nests + t.nest);
+    int32_t* dst = reinterpret_cast<int32_t*>(&e.bn);
+    for (int i = lane; i < static_cast<int>(sizeof(BatchNest) / 4); i += 32) dst[i] = src[i];
+  }
+  // a consumer wait for the next tile that gave up
+  __device__ __forceinline__ void report(int32_t code) const {
+    if (nests[0].err) atomicExch(nests[0].err, code);
+  }
+  __device__ __forceinline__ unsigned long long idle_limit_ns() const { return kBatchWaitNs; }
+  __device__ __forceinline__ void tile_done(const BatchQueued&, uint32_t) const {}
+};
+
 // ---------------------------------------------------------------- producer warp
-__device__ __forceinline__ void batch_producer(const BatchNest* __restrict__ nests,
-                                               const BatchTile* __restrict__ tiles, int64_t n_tiles,
-                                               unsigned long long* counter, BatchQueued* tq, uint32_t ring,
-                                               uint32_t full, uint32_t empty, uint32_t tq_full, uint32_t tq_empty,
+template <class Src>
+__device__ __forceinline__ void batch_producer(const Src& src, BatchQueued* tq, uint32_t ring, uint32_t full,
+                                               uint32_t empty, uint32_t tq_full, uint32_t tq_empty,
                                                uint32_t abort_at) {
   const int lane = threadIdx.x & 31;
   int64_t kst = 0;   // stages issued so far
@@ -758,21 +785,18 @@ __device__ __forceinline__ void batch_producer(const BatchNest* __restrict__ nes
     int ok = 1;
     if (lane == 0) ok = mbar_wait(tq_empty + 8u * s, static_cast<uint32_t>(((q / kTileQueue) & 1) ^ 1), abort_at);
     if (!__shfl_sync(~0u, ok, 0)) break;   // consumers gave up: they leave at their next tile boundary
-    unsigned long long k = 0;
-    if (lane == 0) k = atomicAdd(counter, 1ull);
+    long long k = 0;
+    if (lane == 0) k = src.claim();
     k = __shfl_sync(~0u, k, 0);
+    if constexpr (Src::kResident) __syncwarp();   // lane 0's acquire of the tile orders the warp's reads
     BatchQueued& e = tq[s];
-    if (static_cast<int64_t>(k) >= n_tiles) {
+    if (k < 0) {
       if (lane == 0) e.end = 1;
       mbar_arrive(tq_full + 8u * s);
       break;
     }
-    const BatchTile t = tiles[k];
-    {
-      const int32_t* src = reinterpret_cast<const int32_t*>(nests + t.nest);
-      int32_t* dst = reinterpret_cast<int32_t*>(&e.bn);
-      for (int i = lane; i < static_cast<int>(sizeof(BatchNest) / 4); i += 32) dst[i] = src[i];
-    }
+    const BatchTile t = src.tile(k);
+    src.desc(lane, t, e);
     __syncwarp();
     const RectPlan& p = e.bn.rp;
     int64_t nst = 0;
@@ -808,10 +832,10 @@ __device__ __forceinline__ void batch_producer(const BatchNest* __restrict__ nes
           nst = i;   // stages not issued are never waited for (the CTA is aborting)
           break;
         }
-        const uint64_t src = a0 + static_cast<uint64_t>(i) * kStageBytes;
-        const uint32_t bytes = static_cast<uint32_t>(a1 - src < kStageBytes ? a1 - src : kStageBytes);
+        const uint64_t src_a = a0 + static_cast<uint64_t>(i) * kStageBytes;
+        const uint32_t bytes = static_cast<uint32_t>(a1 - src_a < kStageBytes ? a1 - src_a : kStageBytes);
         mbar_arrive_tx(full + 8u * slot, bytes);
-        bulk_g2s(ring + slot * kStageBytes, src, bytes, full + 8u * slot);
+        bulk_g2s(ring + slot * kStageBytes, src_a, bytes, full + 8u * slot);
       }
     }
     kst += __shfl_sync(~0u, nst, 0);
@@ -823,11 +847,9 @@ __device__ __forceinline__ void batch_producer(const BatchNest* __restrict__ nes
       mbar_wait(full + 8u * static_cast<uint32_t>(kk % kStages), static_cast<uint32_t>((kk / kStages) & 1), 0u);
 }
 
-// ---------------------------------------------------------------- the persistent kernel
-template <class Op>
-__global__ void __launch_bounds__(kBatchAllThreads, HP_BATCH_MIN_BLOCKS)
-    batch_kernel(const BatchNest* __restrict__ nests, const BatchTile* __restrict__ tiles, int64_t n_tiles,
-                 unsigned long long* counter) {
+// ---------------------------------------------------------------- the persistent CTA
+template <class Op, class Src>
+__device__ __forceinline__ void batch_cta(const Src& src) {
   using Acc = typename Op::Acc;
   using In = typename Op::In;
   extern __shared__ __align__(128) unsigned char batch_ring[];
@@ -852,15 +874,16 @@ __global__ void __launch_bounds__(kBatchAllThreads, HP_BATCH_MIN_BLOCKS)
   }
   __syncthreads();
   if (threadIdx.x >= kBatchThreads) {
-    batch_producer(nests, tiles, n_tiles, counter, tq, ring, full, empty, tq_full, tq_empty, abort_at);
+    batch_producer(src, tq, ring, full, empty, tq_full, tq_empty, abort_at);
     return;
   }
   int64_t ready = 0, rel = 0;
   for (int64_t q = 0;; ++q) {
     const int s = static_cast<int>(q % kTileQueue);
-    if (!mbar_wait(tq_full + 8u * s, static_cast<uint32_t>((q / kTileQueue) & 1), abort_at) && !ld_abort(abort_at)) {
+    if (!mbar_wait(tq_full + 8u * s, static_cast<uint32_t>((q / kTileQueue) & 1), abort_at, src.idle_limit_ns()) &&
+        !ld_abort(abort_at)) {
       st_abort(abort_at);
-      if (nests[0].err) atomicExch(nests[0].err, kErrStageWait);
+      src.report(kErrStageWait);
     }
     if (consumer_sync_or(ld_abort(abort_at))) break;   // one decision for all consumer warps
     const BatchQueued& e = tq[s];
@@ -893,8 +916,16 @@ __global__ void __launch_bounds__(kBatchAllThreads, HP_BATCH_MIN_BLOCKS)
         }
       }
     }
+    if constexpr (Src::kResident) src.tile_done(e, abort_at);
     mbar_arrive(tq_empty + 8u * s);   // this thread is done with the entry
   }
+}
+
+template <class Op>
+__global__ void __launch_bounds__(kBatchAllThreads, HP_BATCH_MIN_BLOCKS)
+    batch_kernel(const BatchNest* __restrict__ nests, const BatchTile* __restrict__ tiles, int64_t n_tiles,
+                 unsigned long long* counter) {
+  batch_cta<Op>(TableSource{nests, tiles, n_tiles, counter});
 }
 
 // host-side launch of one arithmetic's persistent kernel (batch_f32.cu, batch_int.cu)

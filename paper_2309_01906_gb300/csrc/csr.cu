@@ -12,7 +12,7 @@
 //   class 4  longer        chunks of 16384 entries, a CTA per chunk writing
 //                          its partial to the chunk's slot; a second kernel
 //                          folds each row's partials in chunk order (GRID,
-//                          two-pass; FP64 for compensated sums).
+//                          two-pass; double-float for compensated sums).
 // Within a class, lane t of a row's team folds entries start + t + k*L (L the
 // team's lanes) into 4 accumulators (k mod 4), then the team combines them in
 // a fixed tree; the tree depends on the row's length only, never on which
@@ -537,7 +537,7 @@ __global__ void __launch_bounds__(kCsrCtaThreads, HP_CSR_MIN_BLOCKS) csr_split_k
 
 // the second pass of long rows (Sec. 2's recursive reduction at grid level):
 // the thread of a row's first slot folds the row's chunk partials in chunk
-// order (FP64 for compensated sums, rounded once), a fixed tree per row
+// order with the grid-part combine (combine_parts), a fixed tree per row
 template <class Op>
 __global__ void csr_split_combine_kernel(float* __restrict__ y, const int64_t* counters,
                                          const int32_t* __restrict__ chunk_row, const int32_t* __restrict__ chunk_idx,
@@ -549,19 +549,7 @@ __global__ void csr_split_combine_kernel(float* __restrict__ y, const int64_t* c
     if (chunk_idx[k] != 0) continue;
     const int n = chunk_cnt[k];
     if (n < 1 || k + n > n_slots) continue;   // a row the binning could not place whole (flagged there)
-    if constexpr (sizeof(typename Op::Acc) == 8 && Op::kFp) {
-      double sum = 0.0;
-      for (int q = 0; q < n; ++q) {
-        const f2 v = part[k + q];
-        sum += static_cast<double>(v.s);
-        sum += static_cast<double>(v.c);
-      }
-      y[chunk_row[k]] = static_cast<float>(sum);
-    } else {
-      typename Op::Acc v = part[k];
-      for (int q = 1; q < n; ++q) v = Op::combine(v, part[k + q]);
-      y[chunk_row[k]] = Op::finish(v);
-    }
+    y[chunk_row[k]] = combine_parts<Op>(part + k, n, nullptr);
   }
 }
 

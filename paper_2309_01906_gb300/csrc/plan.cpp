@@ -544,7 +544,8 @@ namespace hp {
 //   plain FP32: gamma_k with k = the longest chain of roundings one term goes
 //   through (its thread's sequential share, the vector fold, the lane
 //   butterfly, the warp / rank / grid-part folds);
-//   compensated FP32 (Dot2): u + gamma_k^2, plus the FP64 grid combine.
+//   compensated FP32 (Dot2): u + gamma_k^2, plus, with G > 1 grid parts, the
+//   double-float part combine's gamma_2G (gamma_G + 2 gamma_k).
 double error_bound_rect(const NestPlan& p) {
   const RectPlan& rp = p.rp;
   if (p.prec == HP_I32 || p.prec == HP_I64 || p.op != HP_RED_SUM || rp.team == TEAM_MAP) return 0.0;
@@ -560,7 +561,12 @@ double error_bound_rect(const NestPlan& p) {
   if (p.prec == HP_F32) k += rp.G;
   const double g = (k * u) / (1.0 - k * u);
   if (p.prec == HP_F32) return g;
-  return u + g * g + static_cast<double>(rp.G) * std::ldexp(1.0, -52);
+  double combine = 0.0;
+  if (rp.G > 1) {
+    const auto gamma = [&](double n) { return (n * u) / (1.0 - n * u); };
+    combine = gamma(2.0 * rp.G) * (gamma(static_cast<double>(rp.G)) + 2.0 * g);
+  }
+  return u + g * g + combine;
 }
 
 }  // namespace hp

@@ -13,8 +13,9 @@
 //                      xor-shuffle with width L.
 // When the first reduced level is bound to the grid, every output is cut into
 // G parts that write partials; rect_combine_kernel folds them in part order
-// (FP64 for compensated sums).  The reduction tree depends only on the plan,
-// never on which SM ran what, so runs are bit-reproducible.
+// (combine_parts; compensated partials as a double-float sum).
+// The reduction tree depends only on the plan, never on which SM ran what, so
+// runs are bit-reproducible.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -546,26 +547,8 @@ template <class Op>
 __global__ void rect_combine_kernel(int64_t O, int32_t G, const typename Op::Acc* part, typename Op::Out* out,
                                     float* comp) {
   for (int64_t o = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; o < O;
-       o += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const typename Op::Acc* pp = part + o * G;
-    if constexpr (sizeof(typename Op::Acc) == 8 && Op::kFp) {
-      // compensated FP32 partials: the final grid-level combine runs in FP64
-      double s = 0.0;
-      for (int g = 0; g < G; ++g) {
-        const f2 v = *reinterpret_cast<const f2*>(pp + g);
-        s += static_cast<double>(v.s);
-        s += static_cast<double>(v.c);
-      }
-      const float r = static_cast<float>(s);
-      out[o] = r;
-      // the FP64 remainder, rounded once (out + comp carries the FP64 sum to ~2^-48)
-      if (comp) comp[o] = static_cast<float>(s - static_cast<double>(r));
-    } else {
-      typename Op::Acc a = pp[0];
-      for (int g = 1; g < G; ++g) a = Op::combine(a, pp[g]);
-      out[o] = Op::finish(a);
-    }
-  }
+       o += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    out[o] = combine_parts<Op>(part + o * G, G, comp ? comp + o : nullptr);
 }
 
 // ---------------------------------------------------------------- no reduction: one output per iteration

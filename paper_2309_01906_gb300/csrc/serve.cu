@@ -37,6 +37,7 @@
 #include "api_internal.h"
 #include "batch_kernels.cuh"
 #include "rect_launch.cuh"
+#include "resident_kernels.cuh"
 
 namespace hp {
 
@@ -122,6 +123,49 @@ struct Step {
   unsigned long long* d_counters = nullptr;
 };
 
+// resident mode: one kernel instance at a time takes new tiles (two alternate)
+struct ResidentInst {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ended = nullptr;
+  unsigned long long* d_dev = nullptr;   // claim counter and mirrored tail / stop words
+  bool running = false;                  // launched; its end not yet observed
+  bool stopped = false;                  // its stop flag is written
+  uint64_t base = 0;                     // ring index of its first tile
+  double t_start = 0.0;
+};
+
+struct ResidentLive {
+  Request* r;
+  int slot;
+  uint32_t seq;
+  uint64_t t0;         // ring index of the request's first tile
+  double t_admit;      // host time of its admission
+};
+
+struct Resident {
+  int combo = -1;                        // the arithmetic (batch_combo), fixed by the first request
+  int grid = 0;
+  ResidentReq* h_reqs = nullptr;         // mapped page-locked host memory, with device aliases
+  ResidentReq* d_reqs = nullptr;
+  BatchTile* h_ring = nullptr;
+  BatchTile* d_ring = nullptr;
+  ResidentCtl* h_ctl = nullptr;
+  ResidentCtl* d_ctl = nullptr;
+  uint32_t* h_done = nullptr;
+  uint32_t* d_done = nullptr;
+  int32_t* h_status = nullptr;
+  int32_t* d_status = nullptr;
+  int32_t* d_counts = nullptr;           // device memory
+  ResidentInst inst[2];
+  int cur = 0;
+  uint64_t ring_next = 0;                // ring index of the next tile written
+  double t_query = 0.0;                  // host time of the last event query
+  std::vector<int> free_slots;
+  std::vector<uint32_t> seq;
+  std::vector<ResidentLive> live;
+  std::vector<BatchTile> tiles;          // scratch
+};
+
 }  // namespace
 }  // namespace hp
 
@@ -130,6 +174,8 @@ struct hp_server {
   int max_slots = 0;
   int max_step = 4096;               // requests per step
   bool batching = true;
+  bool resident = false;             // serve_batching 2: a resident kernel takes the tiles
+  hp::Resident res;
   int device = 0, sms = 0;
   std::mutex mu;
   std::condition_variable cv_done;
@@ -281,34 +327,323 @@ hp_status launch_plain(hp_server* s, Step& st) {
   return e == cudaSuccess ? HP_OK : fail(HP_ECUDA, "serve event record");
 }
 
+// a request leaves the server (caller holds the lock)
+void finish_req(hp_server* s, Request* r, bool ok, double t) {
+  r->state = ok ? RQ_DONE : RQ_FAILED;
+  s->bytes_in_flight -= r->bytes;
+  s->slots_used -= 1;
+  if (r->part_bytes) s->part_alloc.release(r->part_off, r->part_bytes);
+  if (r->ticket_bytes) s->ticket_alloc.release(r->ticket_off, r->ticket_bytes);
+  if (ok) {
+    s->lat_us.push_back(t - r->t_submit);
+    s->n_done += 1;
+    s->t_last = t;
+  }
+}
+
 void finish_step(hp_server* s, Step& st, bool ok) {
   const double t = now_us();
   std::lock_guard<std::mutex> lock(s->mu);
-  for (Request* r : st.reqs) {
-    r->state = ok ? RQ_DONE : RQ_FAILED;
-    s->bytes_in_flight -= r->bytes;
-    s->slots_used -= 1;
-    if (r->part_bytes) s->part_alloc.release(r->part_off, r->part_bytes);
-    if (r->ticket_bytes) s->ticket_alloc.release(r->ticket_off, r->ticket_bytes);
-    if (ok) {
-      s->lat_us.push_back(t - r->t_submit);
-      s->n_done += 1;
-      s->t_last = t;
-    }
-  }
+  for (Request* r : st.reqs) finish_req(s, r, ok, t);
   st.reqs.clear();
   st.busy = false;
   s->cv_done.notify_all();
 }
 
+// the device descriptor of an admitted request
+BatchNest batch_nest_of(const hp_server* s, const Request& r) {
+  BatchNest bn;
+  bn.rp = r.nest->plan.rp;
+  bn.in0 = r.in[0];
+  bn.in1 = r.in[1];
+  bn.out = r.out;
+  bn.part = r.part_bytes ? static_cast<char*>(s->part_pool) + r.part_off : nullptr;
+  bn.tickets = r.ticket_bytes ? reinterpret_cast<int32_t*>(reinterpret_cast<char*>(s->ticket_pool) + r.ticket_off)
+                              : nullptr;
+  bn.err = r.nest->err;
+  return bn;
+}
+
 // how long an idle scheduler keeps polling before it sleeps on the condition variable
 constexpr double kServeSpinUs = 2000.0;
+
+// ---------------------------------------------------------------- resident mode
+constexpr double kResidentEpochUs = 100000.0;                 // host time an instance takes new tiles
+constexpr unsigned long long kResidentCapNs = 2000000000ull;  // device bound of one tile wait
+constexpr uint64_t kResidentRing = uint64_t(1) << 16;         // tile ring entries
+constexpr int64_t kResidentTileIters = 8192;                  // iterations per tile, at least
+constexpr int64_t kResidentMaxTiles = 1024;                   // tiles per request, about at most
+constexpr double kResidentLateUs = 10e6;                      // a request not done 10 s after admission fails the server
+
+template <class T>
+bool alloc_mapped(T** h, T** d, size_t n) {
+  *h = nullptr;
+  *d = nullptr;
+  if (cudaHostAlloc(reinterpret_cast<void**>(h), n * sizeof(T), cudaHostAllocMapped) != cudaSuccess) return false;
+  std::memset(static_cast<void*>(*h), 0, n * sizeof(T));
+  return cudaHostGetDevicePointer(reinterpret_cast<void**>(d), *h, 0) == cudaSuccess;
+}
+
+hp_status resident_init(hp_server* s) {
+  Resident& R = s->res;
+  if (!alloc_mapped(&R.h_reqs, &R.d_reqs, s->max_slots) || !alloc_mapped(&R.h_ring, &R.d_ring, kResidentRing) ||
+      !alloc_mapped(&R.h_ctl, &R.d_ctl, 2) || !alloc_mapped(&R.h_done, &R.d_done, s->max_slots) ||
+      !alloc_mapped(&R.h_status, &R.d_status, 2))
+    return fail(HP_ENOMEM, "mapped page-locked memory (resident server tables)");
+  if (cudaMalloc(&R.d_counts, sizeof(int32_t) * s->max_slots) != cudaSuccess ||
+      cudaMemset(R.d_counts, 0, sizeof(int32_t) * s->max_slots) != cudaSuccess)
+    return fail(HP_ENOMEM, "cudaMalloc (resident tile counts)");
+  for (ResidentInst& I : R.inst) {
+    if (cudaStreamCreateWithFlags(&I.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&I.ended, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMalloc(&I.d_dev, sizeof(unsigned long long) * kResidentDevWords) != cudaSuccess)
+      return fail(HP_ECUDA, "resident server streams");
+  }
+  R.free_slots.resize(s->max_slots);
+  for (int i = 0; i < s->max_slots; ++i) R.free_slots[i] = s->max_slots - 1 - i;
+  R.seq.assign(s->max_slots, 0u);
+  return HP_OK;
+}
+
+void resident_free(hp_server* s) {
+  Resident& R = s->res;
+  for (ResidentInst& I : R.inst) {
+    if (I.stream) cudaStreamSynchronize(I.stream);
+    if (I.ended) cudaEventDestroy(I.ended);
+    if (I.stream) cudaStreamDestroy(I.stream);
+    if (I.d_dev) cudaFree(I.d_dev);
+  }
+  if (R.d_counts) cudaFree(R.d_counts);
+  if (R.h_reqs) cudaFreeHost(R.h_reqs);
+  if (R.h_ring) cudaFreeHost(R.h_ring);
+  if (R.h_ctl) cudaFreeHost(R.h_ctl);
+  if (R.h_done) cudaFreeHost(R.h_done);
+  if (R.h_status) cudaFreeHost(R.h_status);
+}
+
+void resident_stop(Resident& R, int i) {
+  if (!R.inst[i].running || R.inst[i].stopped) return;
+  __atomic_store_n(&R.h_ctl[i].stop, 1ull, __ATOMIC_RELEASE);   // after every tail store to it
+  R.inst[i].stopped = true;
+}
+
+hp_status resident_launch(hp_server* s, int i) {
+  Resident& R = s->res;
+  ResidentInst& I = R.inst[i];
+  if (R.grid == 0) {
+    // one CTA per SM fewer than fit: other kernels keep room on every SM
+    const int per_sm = resident_combo_blocks_per_sm(R.combo);
+    R.grid = std::max(1, per_sm > 1 ? per_sm - 1 : 1) * s->sms;
+  }
+  R.h_ctl[i].tail = 0;
+  R.h_ctl[i].stop = 0;
+  R.h_status[i] = 0;
+  ResidentSource src{R.d_reqs, R.d_ring, kResidentRing - 1, R.ring_next, R.d_ctl + i, I.d_dev,
+                     R.d_counts, R.d_done, R.d_status + i, kResidentCapNs};
+  cudaError_t e = cudaMemsetAsync(I.d_dev, 0, sizeof(unsigned long long) * kResidentDevWords, I.stream);
+  if (e == cudaSuccess) e = launch_resident_combo(R.combo, src, R.grid, I.stream);
+  if (e == cudaSuccess) e = cudaEventRecord(I.ended, I.stream);
+  if (e != cudaSuccess) return fail(HP_ECUDA, std::string("resident kernel launch: ") + cudaGetErrorString(e));
+  I.running = true;
+  I.stopped = false;
+  I.base = R.ring_next;
+  I.t_start = now_us();
+  std::lock_guard<std::mutex> lock(s->mu);
+  s->n_steps += 1;
+  return HP_OK;
+}
+
+// every live request fails (an instance ended early or reported an error)
+void resident_fail_all(hp_server* s, const std::string& why) {
+  Resident& R = s->res;
+  const double t = now_us();
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (s->error.empty()) s->error = why;
+  for (const ResidentLive& L : R.live) {
+    finish_req(s, L.r, false, t);
+    R.free_slots.push_back(L.slot);
+  }
+  R.live.clear();
+  s->cv_done.notify_all();
+}
+
+// one pass of the resident scheduler; true when something happened
+bool resident_pass(hp_server* s, double& last_active) {
+  Resident& R = s->res;
+  bool progress = false;
+  // completions, read from the host words the kernel writes
+  if (!R.live.empty()) {
+    const double t = now_us();
+    std::unique_lock<std::mutex> lock(s->mu, std::defer_lock);
+    for (size_t j = 0; j < R.live.size();) {
+      const ResidentLive L = R.live[j];
+      if (__atomic_load_n(&R.h_done[L.slot], __ATOMIC_ACQUIRE) == L.seq) {
+        if (!lock.owns_lock()) lock.lock();
+        finish_req(s, L.r, true, t);
+        R.free_slots.push_back(L.slot);
+        R.live[j] = R.live.back();
+        R.live.pop_back();
+        progress = true;
+      } else {
+        ++j;
+      }
+    }
+    if (progress) s->cv_done.notify_all();
+  }
+  // a device error word, or a request far past any plausible run time: the
+  // server fails its live requests (and refuses new ones)
+  if (!R.live.empty()) {
+    bool bad = false;
+    for (int i = 0; i < 2; ++i)
+      if (R.inst[i].running && __atomic_load_n(&R.h_status[i], __ATOMIC_ACQUIRE) != 0) bad = true;
+    if (bad) {
+      resident_fail_all(s, "resident kernel reported a wait that gave up");
+      progress = true;
+    } else {
+      const double t = now_us();
+      for (const ResidentLive& L : R.live)
+        if (t - L.t_admit > kResidentLateUs) {
+          resident_fail_all(s, "a resident request did not complete within 10 s");
+          progress = true;
+          break;
+        }
+    }
+  }
+  // instances that ended: expected after a stop; otherwise every live request
+  // fails (queried every 20 us: an event query costs about a microsecond)
+  const double t_q = now_us();
+  if (t_q - R.t_query >= 20.0) {
+    R.t_query = t_q;
+    for (int i = 0; i < 2; ++i) {
+      ResidentInst& I = R.inst[i];
+      if (!I.running) continue;
+      const cudaError_t q = cudaEventQuery(I.ended);
+      if (q == cudaErrorNotReady) continue;
+      I.running = false;
+      const int32_t st = __atomic_load_n(&R.h_status[i], __ATOMIC_ACQUIRE);
+      if (q != cudaSuccess || st != 0 || !I.stopped)
+        resident_fail_all(s, q != cudaSuccess ? std::string("resident kernel: ") + cudaGetErrorString(q)
+                                              : "resident kernel ended early (device status " + std::to_string(st) +
+                                                    ")");
+      progress = true;
+    }
+  }
+  bool queued;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    queued = !s->queue.empty() && s->error.empty();
+  }
+  if (queued) {
+    // the instance that takes new tiles: the current one unless it is stopped
+    if (R.inst[R.cur].stopped || !R.inst[R.cur].running) {
+      const int nxt = R.inst[R.cur].stopped ? R.cur ^ 1 : R.cur;
+      if (!R.inst[nxt].running) {
+        R.cur = nxt;
+        if (resident_launch(s, nxt) != HP_OK) {
+          resident_fail_all(s, last_error_string());
+          return true;
+        }
+        progress = true;
+      }
+    }
+    ResidentInst& I = R.inst[R.cur];
+    if (I.running && !I.stopped) {
+      uint64_t low = R.ring_next;
+      for (const ResidentLive& L : R.live) low = std::min(low, L.t0);
+      int admitted = 0;
+      std::vector<Request*> empty;
+      {
+        std::lock_guard<std::mutex> lock(s->mu);
+        while (!s->queue.empty() && s->slots_used < s->max_slots && !R.free_slots.empty()) {
+          Request& r = s->reqs[s->queue.front() - 1];
+          if (s->bytes_in_flight + r.bytes > s->budget) break;
+          const RectPlan& rp = r.nest->plan.rp;
+          const int64_t total = rp.team == TEAM_MAP ? rp.O : rp.O * std::max<int64_t>(1, rp.R);
+          R.tiles.clear();
+          const int slot = R.free_slots.back();
+          step_tiles(slot, rp, std::max(kResidentTileIters, total / kResidentMaxTiles), R.tiles);
+          if (R.ring_next + R.tiles.size() - low > kResidentRing) break;
+          if (r.part_bytes && !s->part_alloc.alloc(r.part_bytes, &r.part_off)) break;
+          if (r.ticket_bytes && !s->ticket_alloc.alloc(r.ticket_bytes, &r.ticket_off)) {
+            if (r.part_bytes) s->part_alloc.release(r.part_off, r.part_bytes);
+            break;
+          }
+          s->queue.pop_front();
+          s->bytes_in_flight += r.bytes;
+          s->slots_used += 1;
+          s->peak_bytes = std::max(s->peak_bytes, s->bytes_in_flight);
+          s->peak_slots = std::max(s->peak_slots, s->slots_used);
+          r.state = RQ_RUNNING;
+          R.free_slots.pop_back();
+          if (R.tiles.empty()) {   // no work items: done at once
+            empty.push_back(&r);
+            R.free_slots.push_back(slot);
+            continue;
+          }
+          const uint32_t sq = ++R.seq[slot] == 0 ? ++R.seq[slot] : R.seq[slot];
+          ResidentReq& d = R.h_reqs[slot];
+          d.bn = batch_nest_of(s, r);
+          d.n_tiles = static_cast<int32_t>(R.tiles.size());
+          d.seq = sq;
+          R.live.push_back({&r, slot, sq, R.ring_next, now_us()});
+          for (const BatchTile& t : R.tiles) R.h_ring[R.ring_next++ & (kResidentRing - 1)] = t;
+          admitted += 1;
+        }
+        const double t = now_us();
+        for (Request* r : empty) finish_req(s, r, true, t);
+        if (!empty.empty()) s->cv_done.notify_all();
+      }
+      if (admitted) {
+        // publish: descriptors and tiles above are written before the tail
+        __atomic_store_n(&R.h_ctl[R.cur].tail, R.ring_next - I.base, __ATOMIC_RELEASE);
+      }
+      if (admitted || !empty.empty()) progress = true;
+    }
+  }
+  if (progress) last_active = now_us();
+  // the current instance stops after its epoch (the next one starts at once
+  // while work is pending) or once the server has been idle for a while
+  ResidentInst& I = R.inst[R.cur];
+  if (I.running && !I.stopped) {
+    const double t = now_us();
+    bool pending;
+    {
+      std::lock_guard<std::mutex> lock(s->mu);
+      pending = !s->queue.empty();
+    }
+    const bool work = !R.live.empty() || pending;
+    if (!work && t - last_active > kServeSpinUs) {
+      resident_stop(R, R.cur);
+    } else if (t - I.t_start > kResidentEpochUs && !R.inst[R.cur ^ 1].running) {
+      resident_stop(R, R.cur);
+      if (work) {   // without work the next admission starts the next instance
+        R.cur ^= 1;
+        if (resident_launch(s, R.cur) != HP_OK) resident_fail_all(s, last_error_string());
+      }
+    }
+  }
+  return progress;
+}
+
 
 void scheduler(hp_server* s) {
   cudaSetDevice(s->device);
   double last_active = now_us();
   while (!s->stop.load(std::memory_order_relaxed)) {
     bool progress = false;
+    if (s->resident) {
+      progress = resident_pass(s, last_active);
+      if (!progress) {
+        if (!s->res.live.empty() || now_us() - last_active < kServeSpinUs) {
+          std::this_thread::yield();
+        } else {
+          std::unique_lock<std::mutex> lock(s->mu);
+          s->cv_work.wait_for(lock, std::chrono::milliseconds(1),
+                              [&] { return !s->queue.empty() || s->stop.load(std::memory_order_relaxed); });
+        }
+      }
+      continue;
+    }
     for (Step& st : s->steps) {
       if (!st.busy) continue;
       const cudaError_t q = cudaEventQuery(st.done);
@@ -396,6 +731,7 @@ hp_status hp_serve_create(size_t mem_budget_bytes, int max_slots, int n_streams,
   s->budget = mem_budget_bytes;
   s->max_slots = max_slots;
   s->batching = options().serve_batching != 0;
+  s->resident = options().serve_batching == 2;
   cudaError_t e = cudaGetDevice(&s->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
   if (e != cudaSuccess) {
@@ -422,6 +758,14 @@ hp_status hp_serve_create(size_t mem_budget_bytes, int max_slots, int n_streams,
       return fail(HP_ECUDA, "serving streams");
     }
   }
+  if (s->resident) {
+    const hp_status h = resident_init(s);
+    if (h != HP_OK) {
+      const std::string why = last_error_string();
+      hp_serve_destroy(s);
+      return fail(h, why);
+    }
+  }
   s->th = std::thread(scheduler, s);
   *out = s;
   return HP_OK;
@@ -439,6 +783,9 @@ hp_status submit(hp_server* s, const hp_nest* shape, const void* const* in_dev, 
   if (s->batching && rp.team == TEAM_BLOCK && (rp.C > 1 || rp.W > kBatchThreads / 32))
     return fail(HP_EUNSUPPORTED, "served block teams are single CTAs of at most 8 warps");
   if (n->plan.body == HP_BODY_GEOMETRIC) return fail(HP_EUNSUPPORTED, "the GEOMETRIC body is not served");
+  const int combo = batch_combo(n->plan.prec, n->plan.op);
+  if (s->resident && !resident_combo_ok(combo))
+    return fail(HP_EUNSUPPORTED, "a resident server runs FP32 and int32 nests");
   hp_status st = ensure_device(n);
   if (st != HP_OK) return st;
   for (int i = 0; i < n->plan.n_inputs; ++i)
@@ -456,6 +803,11 @@ hp_status submit(hp_server* s, const hp_nest* shape, const void* const* in_dev, 
   r.state = RQ_QUEUED;
   std::lock_guard<std::mutex> lock(s->mu);
   if (!s->error.empty()) return fail(HP_ECUDA, s->error);
+  if (s->resident) {
+    if (s->res.combo < 0) s->res.combo = combo;
+    if (s->res.combo != combo)
+      return fail(HP_EUNSUPPORTED, "a resident server runs one arithmetic: its first request's precision and op");
+  }
   const double t = now_us();
   if (arrival_us > t) return fail(HP_EINVAL, "hp_serve_submit_at: the arrival time lies in the future");
   r.t_submit = arrival_us >= 0.0 ? arrival_us : t;
@@ -545,6 +897,11 @@ void hp_serve_destroy(hp_server* s) {
   }
   s->cv_work.notify_all();
   if (s->th.joinable()) s->th.join();
+  if (s->resident) {
+    resident_stop(s->res, 0);
+    resident_stop(s->res, 1);
+    resident_free(s);
+  }
   for (Step& st : s->steps) {
     if (st.stream) cudaStreamSynchronize(st.stream);
     if (st.done) cudaEventDestroy(st.done);

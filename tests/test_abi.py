@@ -158,7 +158,12 @@ def test_serving_needs_a_gpu():
     assert e.status == hb.HP_EINVAL
     hb.hp_set_option("serve_batching", 0)
     assert hb.hp_get_option("serve_batching") == 0
+    hb.hp_set_option("serve_batching", 2)
+    assert hb.hp_get_option("serve_batching") == 2
     hb.hp_set_option("serve_batching", 1)
+    for bad in (-1, 3):
+        assert _err(hb.hp_set_option, "serve_batching", bad).status == hb.HP_EINVAL
+    assert hb.hp_get_option("serve_batching") == 1
 
 
 def _header_enums():
