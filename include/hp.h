@@ -419,7 +419,10 @@ hp_status hp_probe_gather(const float *x_dev, int64_t n_x, int64_t n_gathers, ui
  * with an error status, which fails the server's live requests).  A resident
  * server runs one arithmetic, set by its first request (FP32 sum, compensated
  * sum, max, min or int32 sum, max, min); other requests get HP_EUNSUPPORTED.
- * Other kernels on the GPU share it with the instance while it runs. */
+ * Other kernels on the GPU share it with the instance while it runs.  A
+ * resident server prepares nothing of a submitted nest on the device (its
+ * requests report device errors through the server's own error word), so that
+ * no allocation in hp_serve_submit can wait for the running instance. */
 
 /* mem_budget_bytes: admission budget (inputs + outputs + scratch of admitted
  * requests); max_slots: requests resident at once; n_streams (1..64): CUDA

@@ -397,52 +397,53 @@ __device__ __forceinline__ long long ld_part(const long long* p) { return __ldcg
 // the parts' chain length), far below the FP32 result's rounding.  FP64 is
 // not used: a dependent FP64 operation costs about 63 SM cycles on this GPU
 // (FP32: 4.5), and a chain of 2G of them took about 40 us for G = 304.
-// Loads are issued 8 parts at a time.
+// one fold step of that combine; every executor folds the same steps in the
+// same order
+template <class Op, bool COMP = std::is_same_v<typename Op::Acc, f2>>
+struct PartFold;
 template <class Op>
-__device__ __forceinline__ typename Op::Out combine_parts(const typename Op::Acc* pp, int32_t G, float* rem) {
-  using Acc = typename Op::Acc;
-  constexpr int K = 8;
-  if constexpr (std::is_same_v<Acc, f2>) {
-    float S = 0.0f, C = 0.0f;
-    int32_t g = 0;
-    for (; g + K <= G; g += K) {
-      f2 v[K];
-#pragma unroll
-      for (int k = 0; k < K; ++k) v[k] = ld_part(pp + g + k);
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        float s2, e;
-        two_sum(S, v[k].s, s2, e);
-        S = s2;
-        C = __fadd_rn(C, e);
-        C = __fadd_rn(C, v[k].c);
-      }
-    }
-    for (; g < G; ++g) {
-      const f2 v = ld_part(pp + g);
-      float s2, e;
-      two_sum(S, v.s, s2, e);
-      S = s2;
-      C = __fadd_rn(C, e);
-      C = __fadd_rn(C, v.c);
-    }
+struct PartFold<Op, true> {
+  float S = 0.0f, C = 0.0f;
+  __device__ __forceinline__ void first(const f2& v) { add(v); }
+  __device__ __forceinline__ void add(const f2& v) {
+    float s2, e;
+    two_sum(S, v.s, s2, e);
+    S = s2;
+    C = __fadd_rn(C, e);
+    C = __fadd_rn(C, v.c);
+  }
+  __device__ __forceinline__ float result(float* rem) const {
     float r, e;
     two_sum(S, C, r, e);
     if (rem) *rem = e;
     return r;
-  } else {
-    Acc a = ld_part(pp);
-    int32_t g = 1;
-    for (; g + K <= G; g += K) {
-      Acc v[K];
-#pragma unroll
-      for (int k = 0; k < K; ++k) v[k] = ld_part(pp + g + k);
-#pragma unroll
-      for (int k = 0; k < K; ++k) a = Op::combine(a, v[k]);
-    }
-    for (; g < G; ++g) a = Op::combine(a, ld_part(pp + g));
-    return Op::finish(a);
   }
+};
+template <class Op>
+struct PartFold<Op, false> {
+  typename Op::Acc a;
+  __device__ __forceinline__ void first(const typename Op::Acc& v) { a = v; }
+  __device__ __forceinline__ void add(const typename Op::Acc& v) { a = Op::combine(a, v); }
+  __device__ __forceinline__ typename Op::Out result(float*) const { return Op::finish(a); }
+};
+
+// the combine by one thread, loading 8 parts at a time from L2
+template <class Op>
+__device__ __forceinline__ typename Op::Out combine_parts(const typename Op::Acc* pp, int32_t G, float* rem) {
+  using Acc = typename Op::Acc;
+  constexpr int K = 8;
+  PartFold<Op> f;
+  f.first(ld_part(pp));
+  int32_t g = 1;
+  for (; g + K <= G; g += K) {
+    Acc v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = ld_part(pp + g + k);
+#pragma unroll
+    for (int k = 0; k < K; ++k) f.add(v[k]);
+  }
+  for (; g < G; ++g) f.add(ld_part(pp + g));
+  return f.result(rem);
 }
 
 }  // namespace hp

@@ -543,12 +543,38 @@ __global__ void __launch_bounds__(1024) rect_lanes_kernel(RectPlan p, Body body,
 }
 
 // ---------------------------------------------------------------- grid parts -> outputs
+// A warp per output: the lanes stage up to 256 parts at a time in shared
+// memory with coalesced loads, and lane 0 folds them in part order (the steps
+// of combine_parts, so the bits equal the batched executors').  256 threads.
+constexpr int kCombineWarps = 8;
+constexpr int kCombineChunk = 256;
 template <class Op>
-__global__ void rect_combine_kernel(int64_t O, int32_t G, const typename Op::Acc* part, typename Op::Out* out,
-                                    float* comp) {
-  for (int64_t o = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; o < O;
-       o += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    out[o] = combine_parts<Op>(part + o * G, G, comp ? comp + o : nullptr);
+__global__ void __launch_bounds__(32 * kCombineWarps) rect_combine_kernel(int64_t O, int32_t G,
+                                                                        const typename Op::Acc* part,
+                                                                        typename Op::Out* out, float* comp) {
+  using Acc = typename Op::Acc;
+  __shared__ Acc stage[kCombineWarps][kCombineChunk];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t o = blockIdx.x * static_cast<int64_t>(kCombineWarps) + warp; o < O;
+       o += static_cast<int64_t>(gridDim.x) * kCombineWarps) {
+    const Acc* pp = part + o * G;
+    PartFold<Op> f;
+    for (int32_t c0 = 0; c0 < G; c0 += kCombineChunk) {
+      const int n = G - c0 < kCombineChunk ? G - c0 : kCombineChunk;
+      for (int i = lane; i < n; i += 32) stage[warp][i] = pp[c0 + i];
+      __syncwarp();
+      if (lane == 0) {
+        int i = 0;
+        if (c0 == 0) {
+          f.first(stage[warp][0]);
+          i = 1;
+        }
+        for (; i < n; ++i) f.add(stage[warp][i]);
+      }
+      __syncwarp();
+    }
+    if (lane == 0) out[o] = f.result(comp ? comp + o : nullptr);
+  }
 }
 
 // ---------------------------------------------------------------- no reduction: one output per iteration

@@ -112,7 +112,7 @@ hp_status launch_team(const NestPlan& np, RectPlan rp, LaunchCfg& cfg, const Bod
       if (blocks > max_blocks) blocks = max_blocks;
       cfg.grid = static_cast<int>(blocks < 1 ? 1 : blocks);
     }
-    const int64_t cb = (rp.O + 255) / 256;
+    const int64_t cb = (rp.O + kCombineWarps - 1) / kCombineWarps;   // a warp per output
     cfg.combine_grid = static_cast<int>(cb < 4LL * cfg.sms ? (cb > 0 ? cb : 1) : 4LL * cfg.sms);
     cfg.ready = true;
   }
@@ -153,7 +153,7 @@ hp_status launch_team(const NestPlan& np, RectPlan rp, LaunchCfg& cfg, const Bod
     if (e != cudaSuccess) return cuda_fail(e, "rect_lanes_kernel launch");
   }
   if (rp.G > 1) {
-    rect_combine_kernel<Op><<<cfg.combine_grid, 256, 0, a.stream>>>(rp.O, rp.G, part, out, a.comp);
+    rect_combine_kernel<Op><<<cfg.combine_grid, 32 * kCombineWarps, 0, a.stream>>>(rp.O, rp.G, part, out, a.comp);
     e = cudaPeekAtLastError();
     if (e != cudaSuccess) return cuda_fail(e, "rect_combine_kernel launch");
   }

@@ -156,6 +156,7 @@ struct Resident {
   int32_t* h_status = nullptr;
   int32_t* d_status = nullptr;
   int32_t* d_counts = nullptr;           // device memory
+  int32_t* d_err = nullptr;              // device error word of every served request
   ResidentInst inst[2];
   int cur = 0;
   uint64_t ring_next = 0;                // ring index of the next tile written
@@ -360,7 +361,7 @@ BatchNest batch_nest_of(const hp_server* s, const Request& r) {
   bn.part = r.part_bytes ? static_cast<char*>(s->part_pool) + r.part_off : nullptr;
   bn.tickets = r.ticket_bytes ? reinterpret_cast<int32_t*>(reinterpret_cast<char*>(s->ticket_pool) + r.ticket_off)
                               : nullptr;
-  bn.err = r.nest->err;
+  bn.err = s->resident ? s->res.d_err : r.nest->err;
   return bn;
 }
 
@@ -391,7 +392,8 @@ hp_status resident_init(hp_server* s) {
       !alloc_mapped(&R.h_status, &R.d_status, 2))
     return fail(HP_ENOMEM, "mapped page-locked memory (resident server tables)");
   if (cudaMalloc(&R.d_counts, sizeof(int32_t) * s->max_slots) != cudaSuccess ||
-      cudaMemset(R.d_counts, 0, sizeof(int32_t) * s->max_slots) != cudaSuccess)
+      cudaMemset(R.d_counts, 0, sizeof(int32_t) * s->max_slots) != cudaSuccess ||
+      cudaMalloc(&R.d_err, sizeof(int32_t)) != cudaSuccess || cudaMemset(R.d_err, 0, sizeof(int32_t)) != cudaSuccess)
     return fail(HP_ENOMEM, "cudaMalloc (resident tile counts)");
   for (ResidentInst& I : R.inst) {
     if (cudaStreamCreateWithFlags(&I.stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -414,6 +416,7 @@ void resident_free(hp_server* s) {
     if (I.d_dev) cudaFree(I.d_dev);
   }
   if (R.d_counts) cudaFree(R.d_counts);
+  if (R.d_err) cudaFree(R.d_err);
   if (R.h_reqs) cudaFreeHost(R.h_reqs);
   if (R.h_ring) cudaFreeHost(R.h_ring);
   if (R.h_ctl) cudaFreeHost(R.h_ctl);
@@ -786,8 +789,17 @@ hp_status submit(hp_server* s, const hp_nest* shape, const void* const* in_dev, 
   const int combo = batch_combo(n->plan.prec, n->plan.op);
   if (s->resident && !resident_combo_ok(combo))
     return fail(HP_EUNSUPPORTED, "a resident server runs FP32 and int32 nests");
-  hp_status st = ensure_device(n);
-  if (st != HP_OK) return st;
+  if (s->resident) {
+    // nothing of the nest is prepared on the device: a resident request needs
+    // only its host plan (its error word is the server's), and allocating
+    // here could wait for the running resident kernel
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != s->device || (n->device >= 0 && n->device != s->device))
+      return fail(HP_EINVAL, "the nest, the calling thread and the server must share one device");
+  } else {
+    const hp_status st = ensure_device(n);
+    if (st != HP_OK) return st;
+  }
   for (int i = 0; i < n->plan.n_inputs; ++i)
     if (!in_dev || !in_dev[i]) return fail(HP_EINVAL, "missing device input");
   if (!out_dev && rp.O > 0) return fail(HP_EINVAL, "out_dev is NULL");
