@@ -49,6 +49,9 @@ bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 // from the real device at the first run.
 constexpr int64_t kAssumedSMs = 152;
 constexpr int64_t kMinPart = 16384;   // smallest grid part the planner picks by itself
+#ifndef HP_PLAN_TEAMS_PER_SM
+#define HP_PLAN_TEAMS_PER_SM 4          // block teams per SM a grid split aims at
+#endif
 }  // namespace
 
 Options& options() {
@@ -420,10 +423,12 @@ hp_status plan_rect(int depth, const int64_t* extents, const hp_level_map* map, 
     for (int l = vls[0].first; l <= vls[0].last; ++l)
       if (m[l].tile > 0) tile = m[l].tile;
     if (tile <= 0) {
-      // aim at about two block teams per SM over all outputs, with parts of
+      // aim at about four block teams per SM over all outputs (two left a
+      // 1 GiB single-output sum at 3.7 TB/s, four reach 5.7), with parts of
       // at least kMinPart iterations (a part's reduction tree and its ticket
       // cost about as much as folding a few thousand iterations)
-      int64_t want_parts = std::max<int64_t>(1, (2 * kAssumedSMs + O - 1) / std::max<int64_t>(O, 1));
+      const int64_t teams = HP_PLAN_TEAMS_PER_SM * kAssumedSMs;
+      int64_t want_parts = std::max<int64_t>(1, (teams + O - 1) / std::max<int64_t>(O, 1));
       want_parts = std::min<int64_t>(want_parts, std::max<int64_t>(1, n0 / kMinPart));
       tile = (n0 + want_parts - 1) / std::max<int64_t>(want_parts, 1);
     }

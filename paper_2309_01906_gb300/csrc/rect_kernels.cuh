@@ -569,6 +569,13 @@ __global__ void __launch_bounds__(32 * kCombineWarps) rect_combine_kernel(int64_
           f.first(stage[warp][0]);
           i = 1;
         }
+        for (; i + 8 <= n; i += 8) {   // eight shared-memory loads before their folds
+          Acc v[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) v[k] = stage[warp][i + k];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) f.add(v[k]);
+        }
         for (; i < n; ++i) f.add(stage[warp][i]);
       }
       __syncwarp();
