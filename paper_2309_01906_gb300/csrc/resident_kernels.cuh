@@ -16,10 +16,10 @@
 // where the other waiters read it (eight copies on separate lines, so that
 // hundreds of idle producers do not load one L2 slice).  Every tile runs the
 // batched executor's code unchanged, so results are bit-identical to
-// hp_nest_run.  After a tile the consumer warps fence their writes and count
-// the tile against its request; the CTA that finishes the last tile writes the
-// request's sequence number to the completion word with a system-scope
-// release, which the host polls.
+// hp_nest_run.  After a tile the consumer warps meet at a barrier, one thread
+// fences and counts the tile against its request; the CTA that finishes the
+// last tile fences at system scope and writes the request's sequence number to
+// the completion word, which the host polls.
 //
 // Every wait is bounded.  A producer waits for one tile at most cap_ns
 // (global timer), then records status 4, mirrors a stop to the other waiters
@@ -63,12 +63,6 @@ __device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];\n" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ void max_release_gpu(unsigned long long* p, unsigned long long v) {
-  asm volatile("red.release.gpu.global.max.u64 [%0], %1;\n" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ void st_release_sys(uint32_t* p, uint32_t v) {
-  asm volatile("st.release.sys.global.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
-}
 __device__ __forceinline__ void st_relaxed_sys(int32_t* p, int32_t v) {
   asm volatile("st.relaxed.sys.global.s32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
 }
@@ -102,6 +96,13 @@ struct ResidentSource {
   int32_t* status;               // mapped host memory: 0, kErrStageWait or kErrResidentCap
   unsigned long long cap_ns;     // longest wait for one tile
 
+  // publish a value to every mirror copy (word w of each line): one fence
+  // orders what this thread observed before it, then relaxed maxima
+  __device__ __forceinline__ void mirror_all(int w, unsigned long long v) const {
+    __threadfence();
+#pragma unroll
+    for (int c = 0; c < kResidentMirrors; ++c) atomicMax(dev + kResidentLineWords * (1 + c) + w, v);
+  }
   // lane 0: the next published tile, or -1 once the instance stops (or its cap passes)
   __device__ int64_t claim() const {
     const unsigned long long k = atomicAdd(dev, 1ull);
@@ -111,15 +112,16 @@ struct ResidentSource {
       const unsigned long long seen = ld_acquire_gpu(mirror);
       if (k < seen) return static_cast<int64_t>(k);
       if (k == seen) {
-        // the head waiter: read stop before tail, so that a stop seen here
-        // comes with the final tail
-        const unsigned long long st = ld_acquire_sys(&ctl->stop);
+        // the head waiter polls the host's tail; every 8th poll it reads the
+        // stop flag first and the tail after it, so that a stop seen comes
+        // with the final tail
+        const bool check_stop = (i & 7u) == 0;
+        const unsigned long long st = check_stop ? ld_acquire_sys(&ctl->stop) : 0ull;
         const unsigned long long tl = ld_acquire_sys(&ctl->tail);
-        if (tl > seen)
-          for (int c = 0; c < kResidentMirrors; ++c) max_release_gpu(dev + kResidentLineWords * (1 + c), tl);
+        if (tl > seen) mirror_all(0, tl);
         if (k < tl) return static_cast<int64_t>(k);
         if (st) {
-          for (int c = 0; c < kResidentMirrors; ++c) max_release_gpu(dev + kResidentLineWords * (1 + c) + 1, 1ull);
+          mirror_all(1, 1ull);
           return -1;
         }
       } else if (ld_acquire_gpu(mirror + 1)) {
@@ -129,10 +131,10 @@ struct ResidentSource {
       }
       if ((i & 15u) == 0 && global_ns() > t_end) {
         st_relaxed_sys(status, kErrResidentCap);
-        for (int c = 0; c < kResidentMirrors; ++c) max_release_gpu(dev + kResidentLineWords * (1 + c) + 1, 1ull);
+        mirror_all(1, 1ull);
         return -1;
       }
-      __nanosleep(k == seen ? 32u : 256u);
+      if (k != seen) __nanosleep(256u);
     }
   }
   __device__ __forceinline__ BatchTile tile(int64_t k) const {
@@ -144,29 +146,41 @@ struct ResidentSource {
                                    static_cast<uint32_t>(v.z));
     return t;
   }
+  // the slot's descriptor and (n_tiles, seq): 45 words of 8 bytes, every load
+  // issued before the first store, so the host link is crossed once
   __device__ __forceinline__ void desc(int lane, const BatchTile& t, BatchQueued& e) const {
+    constexpr int kWords = static_cast<int>(sizeof(BatchNest) / 8);
     const int2* src = reinterpret_cast<const int2*>(reqs + t.nest);
     int2* dst = reinterpret_cast<int2*>(&e.bn);
-    for (int i = lane; i < static_cast<int>(sizeof(BatchNest) / 8); i += 32) dst[i] = ld_volatile2(src + i);
-    if (lane == 0) {
-      const int2 tail = ld_volatile2(reinterpret_cast<const int2*>(&reqs[t.nest].n_tiles));
-      e.req_tiles = tail.x;
-      e.req_seq = static_cast<uint32_t>(tail.y);
+    const int2 v0 = ld_volatile2(src + lane);
+    const bool two = lane + 32 <= kWords;   // word kWords is (n_tiles, seq)
+    int2 v1 = make_int2(0, 0);
+    if (two) v1 = ld_volatile2(src + lane + 32);
+    dst[lane] = v0;
+    if (two) {
+      if (lane + 32 < kWords) {
+        dst[lane + 32] = v1;
+      } else {
+        e.req_tiles = v1.x;
+        e.req_seq = static_cast<uint32_t>(v1.y);
+      }
     }
   }
   __device__ __forceinline__ void report(int32_t code) const { st_relaxed_sys(status, code); }
   __device__ __forceinline__ unsigned long long idle_limit_ns() const { return cap_ns + kBatchWaitNs; }
   // all consumer threads, after a tile: count it against its request; the
   // last tile of a request publishes the request's completion to the host
+  // (the barrier orders every consumer's writes before thread 0's fence, and
+  // fences are cumulative: one fence per tile publishes the whole CTA's)
   __device__ __forceinline__ void tile_done(const BatchQueued& e, uint32_t abort_at) const {
-    __threadfence();   // this thread's outputs, partials and tickets are visible GPU-wide
     const bool aborted = consumer_sync_or(ld_abort(abort_at));
     if (!aborted && threadIdx.x == 0) {
       const int32_t slot = e.t.nest;
+      __threadfence();   // the CTA's outputs, partials and tickets are visible GPU-wide
       if (atomicAdd(&counts[slot], 1) == e.req_tiles - 1) {
         counts[slot] = 0;   // ready for the slot's next request
         __threadfence_system();
-        st_release_sys(done + slot, e.req_seq);
+        st_relaxed_sys(reinterpret_cast<int32_t*>(done + slot), static_cast<int32_t>(e.req_seq));
       }
     }
   }
