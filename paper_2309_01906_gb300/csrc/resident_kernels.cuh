@@ -33,6 +33,9 @@
 
 namespace hp {
 
+#ifndef HP_RESIDENT_NAP_NS
+#define HP_RESIDENT_NAP_NS 256u                  // a waiter's pause between reads of its mirror copy
+#endif
 constexpr int kResidentMirrors = 8;              // copies of the mirrored tail / stop words
 constexpr int kResidentLineWords = 16;           // one 128-byte line per copy
 constexpr int kResidentDevWords = kResidentLineWords * (1 + kResidentMirrors);
@@ -134,7 +137,7 @@ struct ResidentSource {
         mirror_all(1, 1ull);
         return -1;
       }
-      if (k != seen) __nanosleep(256u);
+      if (k != seen) __nanosleep(HP_RESIDENT_NAP_NS);
     }
   }
   __device__ __forceinline__ BatchTile tile(int64_t k) const {

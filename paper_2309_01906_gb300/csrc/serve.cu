@@ -369,6 +369,9 @@ BatchNest batch_nest_of(const hp_server* s, const Request& r) {
 constexpr double kServeSpinUs = 2000.0;
 
 // ---------------------------------------------------------------- resident mode
+#ifndef HP_RESIDENT_CTAS_PER_SM
+#define HP_RESIDENT_CTAS_PER_SM 0                             // resident CTAs per SM (0: one fewer than fit)
+#endif
 constexpr double kResidentEpochUs = 100000.0;                 // host time an instance takes new tiles
 constexpr unsigned long long kResidentCapNs = 2000000000ull;  // device bound of one tile wait
 constexpr uint64_t kResidentRing = uint64_t(1) << 16;         // tile ring entries
@@ -436,7 +439,8 @@ hp_status resident_launch(hp_server* s, int i) {
   if (R.grid == 0) {
     // one CTA per SM fewer than fit: other kernels keep room on every SM
     const int per_sm = resident_combo_blocks_per_sm(R.combo);
-    R.grid = std::max(1, per_sm > 1 ? per_sm - 1 : 1) * s->sms;
+    const int use = HP_RESIDENT_CTAS_PER_SM > 0 ? std::min(HP_RESIDENT_CTAS_PER_SM, per_sm) : per_sm - 1;
+    R.grid = std::max(1, use) * s->sms;
   }
   R.h_ctl[i].tail = 0;
   R.h_ctl[i].stop = 0;
@@ -768,6 +772,15 @@ hp_status hp_serve_create(size_t mem_budget_bytes, int max_slots, int n_streams,
       hp_serve_destroy(s);
       return fail(h, why);
     }
+  }
+  // load the persistent kernels now (their attributes and occupancy queries
+  // load the code): a first launch that loads them took about 3 ms, which the
+  // first requests would wait for
+  if (s->resident) {
+    for (int c = 0; c < kBatchCombos; ++c)
+      if (resident_combo_ok(c)) (void)resident_combo_blocks_per_sm(c);
+  } else if (s->batching) {
+    for (int c = 0; c < kBatchCombos; ++c) (void)batch_combo_blocks_per_sm(c);
   }
   s->th = std::thread(scheduler, s);
   *out = s;
