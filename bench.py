@@ -1162,9 +1162,14 @@ def serve_measure(args):
                    "sampled_bit_identical_to_single_runs": bool(same)})
         return st, own
 
-    resident, own_r = serve(2)
-    batched, own_b = serve(1)
-    plain, _ = serve(0)
+    modes = [int(m) for m in args.serve_modes.split(",")]
+    skipped = {"skipped": "not in --serve-modes", "p50_us": 0.0, "p99_us": 0.0, "p999_us": 0.0,
+               "sampled_bit_identical_to_single_runs": True}
+    resident, own_r = serve(2) if 2 in modes else (dict(skipped), None)
+    batched, own_b = serve(1) if 1 in modes else (dict(skipped), None)
+    plain, own_p = serve(0) if 0 in modes else (dict(skipped), None)
+    if own_r is None:
+        own_r = own_b if own_b is not None else own_p
     # CPU-baseline leg: the oracle on every distinct sampled nest; the served outputs against it
     parity, cpu = None, None
     if not args.no_cpu_baseline:
@@ -1198,8 +1203,8 @@ def serve_measure(args):
         "metric": "latency from scheduled arrival (us) and nests/s",
         "mean_iterations_per_request": iters, "offered_gbs": args.serve_rate * iters * 4 / 1e9,
         "resident": resident, "batched": batched, "plain_per_request": plain,
-        "p99_speedup": plain["p99_us"] / resident["p99_us"] if resident["p99_us"] else None,
-        "p99_speedup_launched_batches": plain["p99_us"] / batched["p99_us"] if batched["p99_us"] else None,
+        "p99_speedup": plain["p99_us"] / resident["p99_us"] if resident["p99_us"] and plain["p99_us"] else None,
+        "p99_speedup_launched_batches": plain["p99_us"] / batched["p99_us"] if batched["p99_us"] and plain["p99_us"] else None,
         "parity": parity, "cpu_baseline": cpu, "setup_s": setup_s}
     for n, _, _, _ in pool:
         n.close()
@@ -1245,6 +1250,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=None,
                     help="serve: seconds of arrivals (60 for --workload serve, 10 inside the headline line)")
     ap.add_argument("--serve-pool", type=int, default=2000)
+    ap.add_argument("--serve-modes", default="2,1,0",
+                    help="serve: servers to run (2 resident kernel, 1 batched launches, 0 plain launches)")
     ap.add_argument("--no-hist", action="store_true", help="csr: SpMV without the fused histogram")
     ap.add_argument("--extras", default="gemv,csr,batch,serve",
                     help="nest4: other workloads measured after the headline and added to its line "
