@@ -33,6 +33,7 @@ from __future__ import annotations
 
 import argparse
 import ctypes
+import gc
 import json
 import os
 import subprocess
@@ -1135,18 +1136,28 @@ def serve_measure(args):
         ticket = ctypes.c_uint64()
         ticket_ref = ctypes.byref(ticket)
         ks = [int(k) for k in pick]
+        t_arrs = (arrivals * 1e6).tolist()
+        lag = [0.0] * arrivals.size
         torch.cuda.synchronize()
         clock = hb.lib().hp_serve_clock_us
-        t0 = clock()
-        for j, t_arr in enumerate(arrivals.tolist()):
-            due = t0 + t_arr * 1e6
-            now = clock()
-            while now < due:
+        # the garbage collector stays off while the stream runs: its full passes
+        # over the process's objects stalled this client thread for up to 143 ms
+        gc.collect()
+        gc.disable()
+        try:
+            t0 = clock()
+            for j in range(arrivals.size):
+                due = t0 + t_arrs[j]
                 now = clock()
-            lags[j] = now - due
-            k = ks[j]
-            if submit_at(server, handles[k], in_arrs[k], out_ptrs[j], due, ticket_ref) != 0:
-                raise RuntimeError("hp_serve_submit_at: " + hb.hp_last_error())
+                while now < due:
+                    now = clock()
+                lag[j] = now - due
+                k = ks[j]
+                if submit_at(server, handles[k], in_arrs[k], out_ptrs[j], due, ticket_ref) != 0:
+                    raise RuntimeError("hp_serve_submit_at: " + hb.hp_last_error())
+        finally:
+            gc.enable()
+        lags[:] = lag
         hb.hp_serve_poll(server, ticket.value, -1)
         deadline = time.perf_counter() + 120
         while hb.hp_serve_counters(server)["completed"] < arrivals.size and time.perf_counter() < deadline:

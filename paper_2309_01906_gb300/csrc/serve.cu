@@ -192,7 +192,7 @@ struct hp_server {
   size_t part_cap = 0, ticket_cap = 0;
   hp::RangeAlloc part_alloc, ticket_alloc;
   // statistics
-  std::vector<double> lat_us;
+  std::deque<double> lat_us;         // grows by small blocks: no large copy under the lock
   double t_first = 0.0, t_last = 0.0;
   uint64_t n_done = 0;
   uint64_t n_steps = 0;
@@ -887,7 +887,7 @@ hp_status hp_serve_stats(const hp_server* cs, double* p50, double* p99, double* 
   uint64_t n;
   {
     std::lock_guard<std::mutex> lock(s->mu);
-    v = s->lat_us;
+    v.assign(s->lat_us.begin(), s->lat_us.end());
     t0 = s->t_first;
     t1 = s->t_last;
     n = s->n_done;
