@@ -11,7 +11,16 @@
 // admits more.  While steps are in flight, and for 2 ms after the last
 // activity, the scheduler polls without sleeping (it owns one host core);
 // idle longer, it waits on a condition variable that hp_serve_submit signals.
-// No device code waits on anything.
+// In these launched forms no device code waits on anything.
+//
+// Resident form (serve_batching 2): instead of launching steps, the scheduler
+// keeps one instance of the batched persistent kernel running while there is
+// work (resident_kernels.cuh) and hands it each admitted request through
+// mapped page-locked host memory: a slot descriptor, the request's tiles in a
+// ring, then the instance's tail.  The kernel writes each finished request's
+// sequence number to the slot's completion word, which the scheduler polls.
+// Instances take new tiles for one epoch of host time and are stopped and
+// replaced on a second stream; their device waits are bounded.
 //
 // Every request runs its nest's own plan with the single-run reduction tree
 // (the batched kernels are bit-identical to hp_nest_run), so a result does not
