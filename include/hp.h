@@ -465,8 +465,9 @@ hp_status hp_serve_poll(hp_server *s, uint64_t ticket, int timeout_us);
 hp_status hp_serve_stats(const hp_server *s, double *p50_us, double *p99_us, double *p999_us,
                          double *nests_per_s);
 
-/* Counters: completed requests, launched steps, peak admitted bytes and peak
- * admitted requests (both stay within the budget and max_slots). */
+/* Counters: completed requests, launched steps (resident form: kernel
+ * instances started), peak admitted bytes and peak admitted requests (both
+ * stay within the budget and max_slots). */
 hp_status hp_serve_counters(const hp_server *s, uint64_t *completed, uint64_t *steps, size_t *peak_bytes,
                             int32_t *peak_slots);
 
