@@ -28,6 +28,10 @@ namespace hp {
 
 namespace cg = cooperative_groups;
 
+#ifndef HP_FOLD_LOADS
+#define HP_FOLD_LOADS 4   // loads a thread issues before folding them (plain-load kernels)
+#endif
+
 // ---------------------------------------------------------------- loads
 __device__ __forceinline__ float4 ld_stream4(const float* p) { return __ldcs(reinterpret_cast<const float4*>(p)); }
 __device__ __forceinline__ int4 ld_stream4(const int32_t* p) { return __ldcs(reinterpret_cast<const int4*>(p)); }
@@ -194,17 +198,15 @@ __device__ __forceinline__ void fold_item(const RectPlan& p, const Body& body, i
     for (int v = 0; v < last; ++v) roff += x[v] * p.vstride[v];
     const int64_t base = obase + roff;
     if constexpr (Body::kPipeable) {
-      // four loads in flight before the first of their folds (same fold order)
+      // HP_FOLD_LOADS loads in flight before the first of their folds (same fold order)
+      constexpr int NL = HP_FOLD_LOADS;
       int64_t xi = in_lo;
-      for (; xi + 3 * P < in_hi; xi += 4 * P) {
-        const auto v0 = body.template load<V>(base + xi, roff + xi);
-        const auto v1 = body.template load<V>(base + xi + P, roff + xi + P);
-        const auto v2 = body.template load<V>(base + xi + 2 * P, roff + xi + 2 * P);
-        const auto v3 = body.template load<V>(base + xi + 3 * P, roff + xi + 3 * P);
-        body.template apply<V>(acc, v0);
-        body.template apply<V>(acc, v1);
-        body.template apply<V>(acc, v2);
-        body.template apply<V>(acc, v3);
+      for (; xi + (NL - 1) * P < in_hi; xi += NL * P) {
+        decltype(body.template load<V>(base, roff)) v[NL];
+#pragma unroll
+        for (int q = 0; q < NL; ++q) v[q] = body.template load<V>(base + xi + q * P, roff + xi + q * P);
+#pragma unroll
+        for (int q = 0; q < NL; ++q) body.template apply<V>(acc, v[q]);
       }
       for (; xi < in_hi; xi += P) body.template fold<V>(acc, base + xi, roff + xi);
     } else {
