@@ -1137,11 +1137,13 @@ def serve_measure(args):
         ticket_ref = ctypes.byref(ticket)
         ks = [int(k) for k in pick]
         t_arrs = (arrivals * 1e6).tolist()
-        lag = [0.0] * arrivals.size
+        lag = np.full(arrivals.size, 1.0)   # written (so its pages are mapped) before the stream
         torch.cuda.synchronize()
         clock = hb.lib().hp_serve_clock_us
         # the garbage collector stays off while the stream runs: its full passes
-        # over the process's objects stalled this client thread for up to 143 ms
+        # over the process's objects stalled this client thread for up to 143 ms;
+        # the loop keeps no object per request alive (the lags go to a float
+        # array), so it allocates no new memory while the stream runs
         gc.collect()
         gc.disable()
         try:

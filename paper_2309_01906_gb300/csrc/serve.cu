@@ -201,7 +201,7 @@ struct hp_server {
   size_t part_cap = 0, ticket_cap = 0;
   hp::RangeAlloc part_alloc, ticket_alloc;
   // statistics
-  std::deque<double> lat_us;         // grows by small blocks: no large copy under the lock
+  std::vector<double> lat_us;        // reserved and touched at creation: no copy or page fault under the lock
   double t_first = 0.0, t_last = 0.0;
   uint64_t n_done = 0;
   uint64_t n_steps = 0;
@@ -749,6 +749,13 @@ hp_status hp_serve_create(size_t mem_budget_bytes, int max_slots, int n_streams,
   if (!s) return fail(HP_ENOMEM, "host allocation failed");
   s->budget = mem_budget_bytes;
   s->max_slots = max_slots;
+  try {
+    s->lat_us.resize(size_t(1) << 21);   // 16 MB: 2M latencies before the vector must grow
+    s->lat_us.clear();
+  } catch (...) {
+    delete s;
+    return fail(HP_ENOMEM, "host allocation failed");
+  }
   s->batching = options().serve_batching != 0;
   s->resident = options().serve_batching == 2;
   cudaError_t e = cudaGetDevice(&s->device);
@@ -896,7 +903,7 @@ hp_status hp_serve_stats(const hp_server* cs, double* p50, double* p99, double* 
   uint64_t n;
   {
     std::lock_guard<std::mutex> lock(s->mu);
-    v.assign(s->lat_us.begin(), s->lat_us.end());
+    v = s->lat_us;
     t0 = s->t_first;
     t1 = s->t_last;
     n = s->n_done;
