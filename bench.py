@@ -340,6 +340,10 @@ def run_hp(args):
     workloads = {}
     if rank == 0 and ws == 1:   # replicas runs (N > 1) time the headline alone
         for name in [x for x in args.extras.split(",") if x and x != "none"]:
+            # each workload starts from a collected heap and an emptied device cache,
+            # so that host memory freed by the previous one is not reclaimed under it
+            gc.collect()
+            torch.cuda.empty_cache()
             t_w = time.perf_counter()
             workloads[name] = EXTRAS[name](args)
             workloads[name]["wall_s"] = time.perf_counter() - t_w
@@ -1266,9 +1270,11 @@ def main():
     ap.add_argument("--serve-modes", default="2,1,0",
                     help="serve: servers to run (2 resident kernel, 1 batched launches, 0 plain launches)")
     ap.add_argument("--no-hist", action="store_true", help="csr: SpMV without the fused histogram")
-    ap.add_argument("--extras", default="gemv,csr,batch,serve",
+    ap.add_argument("--extras", default="serve,gemv,csr,batch",
                     help="nest4: other workloads measured after the headline and added to its line "
-                         "(comma list of gemv, csr, batch, serve; 'none' for the headline alone)")
+                         "(comma list of serve, gemv, csr, batch, in that order by default: the latency-"
+                         "sensitive serving stream runs before the large CSR and batch workloads; 'none' "
+                         "for the headline alone)")
     ap.add_argument("--parity-out", default="", help="nest4: write the per-result error table (CSV) here")
     ap.add_argument("--batch-check", type=int, default=256, help="batch: nests compared with the oracle")
     ap.add_argument("--batch-plain-steps", type=int, default=3, help="batch: timed passes of one launch per nest")
