@@ -1270,12 +1270,11 @@ def main():
     ap.add_argument("--serve-modes", default="2,1,0",
                     help="serve: servers to run (2 resident kernel, 1 batched launches, 0 plain launches)")
     ap.add_argument("--no-hist", action="store_true", help="csr: SpMV without the fused histogram")
-    ap.add_argument("--extras", default="serve,csr,batch,gemv",
+    ap.add_argument("--extras", default="gemv,serve,csr,batch",
                     help="nest4: other workloads measured after the headline and added to its line "
-                         "(comma list of serve, csr, batch, gemv, in that order by default: the latency-"
-                         "sensitive serving stream runs before the large CSR and batch workloads, and the "
-                         "microsecond GEMV launches after them, on a busy GPU's clocks; 'none' for the "
-                         "headline alone)")
+                         "(comma list of gemv, serve, csr, batch, in that order by default: the latency-"
+                         "sensitive serving stream runs before the large CSR and batch workloads; 'none' "
+                         "for the headline alone)")
     ap.add_argument("--parity-out", default="", help="nest4: write the per-result error table (CSV) here")
     ap.add_argument("--batch-check", type=int, default=256, help="batch: nests compared with the oracle")
     ap.add_argument("--batch-plain-steps", type=int, default=3, help="batch: timed passes of one launch per nest")
