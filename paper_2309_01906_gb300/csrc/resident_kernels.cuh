@@ -39,7 +39,7 @@ namespace hp {
 constexpr int kResidentMirrors = 8;              // copies of the mirrored tail / stop words
 constexpr int kResidentLineWords = 16;           // one 128-byte line per copy
 constexpr int kResidentDevWords = kResidentLineWords * (1 + kResidentMirrors);
-constexpr int32_t kErrResidentCap = 4;           // a producer reached the instance's lifetime cap
+constexpr int32_t kErrResidentCap = 4;           // a producer's wait for one tile reached cap_ns
 
 // per kernel instance, in mapped host memory (written by the host)
 struct ResidentCtl {
@@ -55,6 +55,8 @@ struct alignas(128) ResidentReq {
   uint32_t seq;
 };
 static_assert(sizeof(BatchNest) % 8 == 0 && sizeof(ResidentReq) % 128 == 0, "8-byte copies of whole lines");
+static_assert(sizeof(BatchNest) / 8 >= 32 && sizeof(BatchNest) / 8 + 1 <= 64,
+              "a warp copies a descriptor and its (n_tiles, seq) word in two loads per lane");
 
 __device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long* p) {
   unsigned long long v;

@@ -3,7 +3,11 @@
 A request's result must be the same alone and in a mix of other requests
 (bit for bit: same plan, same reduction tree) and equal hp_nest_run's; the
 budget and slot limits must hold at every moment; the plain per-request mode
-must give the same results."""
+must give the same results.  The resident mode (a persistent kernel fed
+through mapped host memory) is held to the same: bit-identical to hp_nest_run
+alone and in a mix, for FP32 and int32, across instance turnovers and idle
+restarts, with grid-split and thousand-tile requests, within budget and
+slots."""
 import time
 
 import numpy as np
