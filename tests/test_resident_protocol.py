@@ -17,8 +17,14 @@ its copies one at a time).  Invariants checked on every run:
   * every producer ends (the run terminates once stop is set);
   * a producer ends only holding an index at or beyond the final tail.
 
-The model is of the protocol, written here from its description; it shares no
-code with the CUDA source.
+A second model checks the completion side: tiles finishing in any order on
+any CTA, the last one of a request resetting its slot's count and writing the
+request's sequence number, the host recycling slots only after it has seen
+that number.  The host must never see a request done before all its tiles
+are, and every count must return to zero.
+
+The models are of the protocol, written here from its description; they share
+no code with the CUDA source.
 """
 import random
 
@@ -180,3 +186,88 @@ def test_a_planted_mistake_is_caught():
         m.run()
         lost += sorted(m.taken) != list(range(3))
     assert lost > 0
+
+
+class CompletionModel:
+    """The completion side: CTAs count finished tiles per slot; the CTA that
+    counts a request's last tile resets the count and writes the request's
+    sequence number to the slot's completion word; the host reuses a slot only
+    after it has seen that word.  Steps interleave at random."""
+
+    def __init__(self, n_slots, requests, n_ctas, seed):
+        self.rng = random.Random(seed)
+        self.counts = [0] * n_slots
+        self.done = [0] * n_slots
+        self.seq = [0] * n_slots
+        self.free = list(range(n_slots))
+        self.pending = list(requests)         # tile counts of the requests to serve
+        self.queue = []                       # published (slot, seq, n_tiles, tile id)
+        self.finished_tiles = {}              # (slot, seq) -> tiles finished so far
+        self.live = {}                        # slot -> (seq, n_tiles)
+        self.seen_done = []
+        self.ctas = [self._cta() for _ in range(n_ctas)]
+        self.host = self._host()
+
+    def _host(self):
+        while self.pending or self.live:
+            # completions
+            for slot, (sq, n) in list(self.live.items()):
+                if self.done[slot] == sq:
+                    assert self.finished_tiles[(slot, sq)] == n, "completion seen before every tile finished"
+                    self.seen_done.append((slot, sq))
+                    del self.live[slot]
+                    self.free.append(slot)
+                yield
+            # admission
+            if self.pending and self.free:
+                n = self.pending.pop(0)
+                slot = self.free.pop()
+                self.seq[slot] += 1
+                sq = self.seq[slot]
+                self.live[slot] = (sq, n)
+                self.finished_tiles[(slot, sq)] = 0
+                for t in range(n):
+                    self.queue.append((slot, sq, n, t))
+            yield
+
+    def _cta(self):
+        while True:
+            if not self.queue:
+                if not self.pending and not self.live:
+                    return
+                yield
+                continue
+            slot, sq, n, t = self.queue.pop(self.rng.randrange(len(self.queue)))
+            yield                               # the tile runs
+            self.finished_tiles[(slot, sq)] += 1
+            yield                               # barrier, fence
+            old = self.counts[slot]
+            self.counts[slot] = old + 1         # the atomic add
+            yield
+            if old == n - 1:
+                self.counts[slot] = 0
+                yield                           # system fence
+                self.done[slot] = sq
+            yield
+
+    def run(self):
+        actors = [self.host] + self.ctas
+        steps = 0
+        while actors:
+            a = self.rng.choice(actors)
+            try:
+                next(a)
+            except StopIteration:
+                actors.remove(a)
+            steps += 1
+            assert steps < 2_000_000, "did not terminate"
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_completion_is_seen_only_after_every_tile_and_slots_recycle(seed):
+    rng = random.Random(5000 + seed)
+    requests = [rng.choice([1, 1, 2, 3, 8]) for _ in range(rng.randint(1, 40))]
+    m = CompletionModel(n_slots=rng.choice([1, 2, 4]), requests=requests, n_ctas=rng.choice([1, 3, 6]), seed=seed)
+    m.run()
+    assert len(m.seen_done) == len(requests)
+    assert all(c == 0 for c in m.counts)
