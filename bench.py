@@ -11,8 +11,9 @@ One step = one run of the nest (all its launches) over the resident inputs.
 Metric: nest iterations per second (2^29 iterations per step).  The line also
 carries the per-result error of every output the CPU-baseline leg evaluated
 against the FP64 oracle (`parity`), and, after the headline's timed region,
-the GEMV-shaped nest, the ragged CSR nest, the 10,000-nest batch and 10 s of
-Poisson serving (`workloads`; --extras none leaves them out).
+the GEMV-shaped nest, 10 s of Poisson serving (resident, batched-launch and
+plain servers), the ragged CSR nest and the 10,000-nest batch (`workloads`;
+--extras none leaves them out).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hp|reference]
 
@@ -1074,8 +1075,10 @@ def serve_measure(args):
     """Serving: a Poisson stream of nest requests (seed 10) at --serve-rate for
     --serve-seconds; shapes drawn as in the batched workload (seed 9), all FP32
     compensated sums over pre-generated device inputs; 40 GiB admission budget.
-    The same arrival sequence is served by the batched server and by the plain
-    per-request server.  Latency runs from each request's scheduled arrival to
+    The same arrival sequence is served, one after the other, by the resident
+    server (a persistent kernel fed through mapped host memory), the server
+    that launches batched steps and the plain per-request server
+    (--serve-modes).  Latency runs from each request's scheduled arrival to
     the server observing its completion (hp_serve_submit_at), so a client that
     falls behind its schedule counts its lag.  A seeded 1% of the requests
     write to outputs of their own; each is compared bit for bit with a single
